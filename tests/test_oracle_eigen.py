@@ -1,0 +1,128 @@
+"""Pins for the oracle's generalized eigensolvers (Eq. 10-11) and its residual measure.
+
+The dense solver is pinned to closed-form spectra (in test_oracle_graph.py) and to an
+independent LAPACK generalized routine here; the oracle's textbook LOBPCG is pinned to
+the dense solver and to ARPACK shift-invert on larger graphs.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+
+import manifold_graphs as mg
+from oracle import graph_ops as go
+from oracle import eigen as ge
+
+
+@pytest.fixture(scope="module")
+def square1k():
+    return go.from_graph(mg.manifold_graph("square", 1000, 8, 1))
+
+
+@pytest.fixture(scope="module")
+def swiss2k():
+    return go.from_graph(mg.manifold_graph("swiss_roll", 2000, 10, 2))
+
+
+def test_dense_geneig_properties(square1k):
+    ops = square1k
+    res = ge.dense_geneig(ops.A, ops.b, 8)
+    V, lam = res.V, res.lam
+    A = ops.A.toarray()
+    assert np.allclose(V.T @ (ops.b[:, None] * V), np.eye(8), atol=1e-12)
+    assert np.allclose(V.T @ A @ V, np.diag(lam), atol=1e-12)
+    eta = ge.backward_errors(ops.A, ops.b, lam, V)
+    assert np.all(eta < 1e-13)
+    assert np.all(np.diff(lam) >= 0)
+
+
+def test_dense_geneig_matches_lapack_generalized(square1k):
+    ops = square1k
+    res = ge.dense_geneig(ops.A, ops.b, 6)
+    lam_ref, V_ref = sla.eigh(ops.A.toarray(), np.diag(ops.b), subset_by_index=[0, 5])
+    assert np.allclose(res.lam, lam_ref, rtol=1e-12, atol=0)
+    for k in range(6):   # separated eigenvalues: vectors agree up to sign
+        c = abs(res.V[:, k] @ (ops.b * V_ref[:, k]))
+        assert c == pytest.approx(1.0, abs=1e-9)
+
+
+def test_sign_convention():
+    V = np.array([[1.0, -3.0], [-2.0, 3.0], [0.5, 1.0]])
+    F = ge.fix_signs(V)
+    assert F[1, 0] == 2.0          # largest magnitude positive
+    assert F[0, 1] == 3.0          # tie -> lowest index positive
+
+
+@pytest.mark.parametrize("K,guard", [(2, 2), (4, 0), (8, 4)])
+def test_lobpcg_matches_dense(square1k, K, guard):
+    ops = square1k
+    d = ge.dense_geneig(ops.A, ops.b, K + 1)
+    r = ge.lobpcg(ops.A, ops.b, K, guard=guard, tol=1e-12, seed=3)
+    assert r.converged
+    assert np.max(np.abs(r.lam - d.lam[:K]) / d.lam[:K]) < 1e-10
+    assert ge.subspace_angle(r.V, d.V[:, :K]) < 1e-7
+
+
+def test_lobpcg_swiss_roll_matches_dense(swiss2k):
+    ops = swiss2k
+    d = ge.dense_geneig(ops.A, ops.b, 9)
+    r = ge.lobpcg(ops.A, ops.b, 8, guard=2, tol=1e-12, seed=1)
+    assert r.converged
+    assert np.max(np.abs(r.lam - d.lam[:8]) / d.lam[:8]) < 1e-9
+    assert ge.subspace_angle(r.V, d.V[:, :8]) < 1e-6
+
+
+def test_lobpcg_with_constraint_gives_fiedler_value(square1k):
+    ops = square1k
+    n = ops.n
+    Y = np.ones((n, 1)) / np.sqrt(n)
+    r = ge.lobpcg(ops.Q, np.ones(n), 1, guard=3, Y=Y, tol=1e-13, seed=2)
+    assert r.lam[0] == pytest.approx(ops.eps, rel=1e-9)
+
+
+@pytest.mark.slow
+def test_lobpcg_matches_arpack_shift_invert():
+    ops = go.from_graph(mg.manifold_graph("swiss_roll", 6000, 10, 5))
+    import scipy.sparse as sp
+    B = sp.diags(ops.b).tocsc()
+    lam_ref = np.sort(spla.eigsh(ops.A.tocsc(), k=6, M=B, sigma=0.0, which="LM",
+                                 return_eigenvectors=False))
+    r = ge.lobpcg(ops.A, ops.b, 6, guard=2, tol=1e-11, seed=4)
+    assert r.converged
+    assert np.max(np.abs(r.lam - lam_ref) / lam_ref) < 1e-8
+
+
+def test_backward_error_detects_perturbation(square1k):
+    ops = square1k
+    d = ge.dense_geneig(ops.A, ops.b, 3)
+    V = d.V.copy()
+    V[:, 1] += 1e-4 * np.random.default_rng(0).standard_normal(ops.n)
+    eta = ge.backward_errors(ops.A, ops.b, d.lam, V)
+    assert eta[0] < 1e-13 and eta[1] > 1e-7
+
+
+def test_gershgorin_norm_bounds_spectral_norm(square1k):
+    ops = square1k
+    nA = ge.gershgorin_norm(ops.A)
+    top = np.linalg.eigvalsh(ops.A.toarray())[-1]
+    assert top <= nA * (1 + 1e-14)
+
+
+def test_subspace_angle_basic():
+    rng = np.random.default_rng(0)
+    U = rng.standard_normal((50, 3))
+    assert ge.subspace_angle(U, U @ rng.standard_normal((3, 3))) < 1e-12
+    e = np.zeros((50, 1)); e[0] = 1
+    f = np.zeros((50, 1)); f[0] = np.cos(0.01); f[1] = np.sin(0.01)
+    assert ge.subspace_angle(e, f) == pytest.approx(0.01, rel=1e-9)
+
+
+def test_planted_wrong_b_scaling_breaks_generalized_residual(square1k):
+    """Using B^{-1} where B^{-1/2} is needed gives vectors that are not eigenvectors."""
+    ops = square1k
+    s = 1.0 / ops.b
+    C = (ops.A.toarray() * np.sqrt(s)[:, None]) * np.sqrt(s)[None, :]
+    lam, U = np.linalg.eigh(C)
+    V_bad = U[:, :3] * s[:, None]
+    eta = ge.backward_errors(ops.A, ops.b, lam[:3], V_bad)
+    assert np.max(eta) > 1e-6
