@@ -1,0 +1,233 @@
+/*
+ * mge.h -- C ABI of libmge: generalized-eigenvector manifold graph embedding on one GPU.
+ *
+ * The library computes the graph embedding of "Fast computation of Generalized
+ * Eigenvectors for Manifold Graph Embedding" (Chen, Cheung, Zhang): for an input graph
+ * G(V, E, W) it builds the sparse pair
+ *     A = L - mu Q + eps I,   B = diag(b_i)                         (Eq. 6, Sec. 4.3)
+ * and returns the first K generalized eigenpairs A q = lambda B q, q_i^T B q_j = delta_ij
+ * (Eq. 10-11), found by LOBPCG (Sec. 4.3; Knyazev's locally optimal block
+ * preconditioned conjugate gradient method).  All arithmetic runs in the library's own
+ * CUDA kernels for sm_103a; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *   - Errors are returned as mge_status codes; nothing aborts and no C++ exception
+ *     crosses this boundary.  mge_ctx_last_error() gives a one-line message for the last
+ *     failing call on a context.
+ *   - Pointers flagged "host or device" are device pointers when the matching on_device
+ *     flag is nonzero, host pointers otherwise.  Device pointers must belong to the
+ *     context's device.  Caller buffers stay caller-owned; the library never frees them.
+ *   - Handles (mge_ctx, mge_ops) are library-owned and freed by their destroy call.
+ *   - A context is used by one host thread at a time, except mge_submit/mge_poll/
+ *     mge_release, which are thread-safe.
+ *   - Streams are passed as void* (a cudaStream_t); NULL selects the context's stream.
+ *     Calls return after the results they write are complete on the host side.
+ *   - Graph inputs are canonical CSR: row_ptr int64[n+1] with row_ptr[0] = 0, col int32
+ *     strictly ascending within each row, no diagonal entries, weights finite and > 0,
+ *     and the matrix symmetric (W_ij == W_ji bitwise).
+ *   - Block vectors returned to callers (V) are FP64, column-major [n x K].
+ *   - Eigenpairs come out in ascending lambda; each vector's sign is fixed so that its
+ *     entry of largest magnitude is positive (lowest index on ties).
+ */
+#ifndef MGE_H
+#define MGE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MGE_OK = 0,
+  MGE_EINVAL = 1,         /* invalid argument or malformed CSR                              */
+  MGE_ENOTSYM = 2,        /* W is not symmetric                                             */
+  MGE_EISOLATED = 3,      /* some r_i = 0 (isolated node): B is singular (Sec. 4.3)          */
+  MGE_EDEGENERATE = 4,    /* eps = lambda_2(Q) = 0: the two-hop graph is disconnected
+                             (Sec. 4.2); mu = 0 and A = L.  Outputs are still produced.      */
+  MGE_ENOTCONVERGED = 5,  /* maxiter reached; the current Ritz pairs and residuals returned */
+  MGE_ENOMEM = 6,         /* device allocation failed or the HBM budget is exceeded          */
+  MGE_EAGAIN = 7,         /* serving queue or HBM budget full; retry later                   */
+  MGE_ETIMEOUT = 8,       /* mge_poll timed out, or a bounded device loop hit its limit      */
+  MGE_EDEVICE = 9,        /* a CUDA runtime error                                           */
+  MGE_ECHOLESKY = 10,     /* the Rayleigh-Ritz basis collapsed (fewer than m independent
+                             directions): the block is rank deficient                       */
+  MGE_ENOTFOUND = 11,     /* unknown ticket                                                  */
+  MGE_ENOTFINITE = 12     /* a NaN or Inf appeared in the iteration                          */
+} mge_status;
+
+/* Arithmetic of the iterated blocks X, W, P and of the stored matrix values.
+ * Gram accumulation is FP32 (FP64 in MGE_FP64); the Rayleigh-Ritz eigensolve, the
+ * Cholesky factorisations and the residual-norm test are FP64 in every precision. */
+typedef enum { MGE_FP64 = 0, MGE_FP32 = 1, MGE_BF16 = 2 } mge_precision;
+
+typedef struct mge_ctx mge_ctx;
+typedef struct mge_ops mge_ops;
+
+/* ---- context ----------------------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device`.  hbm_budget_bytes bounds the device memory the
+ * context may hold (0 = no limit beyond the device's).  Errors: MGE_EINVAL, MGE_EDEVICE. */
+mge_status mge_create(int device, size_t hbm_budget_bytes, mge_ctx** out);
+mge_status mge_destroy(mge_ctx* ctx);
+const char* mge_strerror(mge_status s);
+const char* mge_ctx_last_error(const mge_ctx* ctx);
+
+typedef struct {
+  uint64_t kernel_launches;   /* kernels this context has launched (graph nodes included)   */
+  uint64_t spmm_launches;     /* SpMM launches recorded while kernel timing was on           */
+  double   spmm_ms;           /* their summed CUDA-event duration                           */
+  uint64_t spmm_bytes;        /* their summed algorithmic bytes                             */
+  size_t   hbm_in_use;        /* bytes of device memory the context holds                   */
+} mge_stats;
+
+/* Copies the context's counters.  mge_ctx_set_timing(ctx, 1) brackets every SpMM launch
+ * with CUDA events (for roofline measurement); 0 turns it off; mge_ctx_reset_stats zeroes. */
+mge_status mge_ctx_stats(const mge_ctx* ctx, mge_stats* out);
+mge_status mge_ctx_set_timing(mge_ctx* ctx, int on);
+mge_status mge_ctx_reset_stats(mge_ctx* ctx);
+
+/* ---- graph operators (Sec. 3.1, Sec. 4.1-4.3) --------------------------------------- */
+
+typedef struct {
+  int      precision;         /* mge_precision of the eps solve and of the stored A values  */
+  int      eps_override_set;  /* nonzero: use eps_override instead of solving lambda_2(Q)   */
+  double   eps_override;
+  int      mu_override_set;   /* nonzero: use mu_override instead of Eq. 9                  */
+  double   mu_override;
+  double   eps_tol;           /* backward-error tolerance of the eps solve (0 = default:
+                                 1e-12 in FP64, 2e-7 in FP32/BF16)                          */
+  int      eps_guard;         /* extra LOBPCG columns for the eps solve (default 3)         */
+  int      eps_maxiter;       /* default 20000                                              */
+  uint64_t seed;              /* seed of the eps solve's initial block                      */
+  void*    stream;            /* cudaStream_t or NULL                                       */
+} mge_ops_opts;
+
+/* Builds the operators of Sec. 4 for the graph W (n nodes, CSR as described above; host
+ * or device pointers per on_device; read only):
+ *   T_i    two-hop sets: j reachable in two hops with (i, j) not an edge (Sec. 4.1.1)
+ *   Q      sum_i Theta_i (Eq. 5), Theta_i = (1/T_i) * Laplacian of the star (i, T_i)
+ *   eps    lambda_2(Q), the Fiedler value, by LOBPCG on (Q, I) with the constant vector
+ *          deflated; 0 when the two-hop graph is disconnected (Sec. 4.2)
+ *   mu     min_i eps / (Q_ii - sum_{j != i} Q_ij) over rows with a positive denominator
+ *          (Eq. 9)
+ *   A      L - mu Q + eps I (Eq. 6) on the structure diag + E + T, ascending columns
+ *   b_i    r_i / (prod_j r_j)^(1/n), r_i the Gershgorin radius of row i of A (Sec. 4.3)
+ * The result is a library-owned handle holding everything on the device.
+ * Errors: MGE_EINVAL (malformed CSR), MGE_ENOTSYM, MGE_EISOLATED, MGE_ENOMEM, MGE_EDEVICE.
+ * MGE_EDEGENERATE is returned together with a valid handle when eps = 0. */
+mge_status mge_build_graph_ops(mge_ctx* ctx, int64_t n, const int64_t* row_ptr,
+                               const int32_t* col, const double* w, int on_device,
+                               const mge_ops_opts* opts, mge_ops** out);
+mge_status mge_ops_destroy(mge_ops* ops);
+
+typedef struct {
+  int64_t n;
+  int64_t nnz_w;              /* entries of W                                               */
+  int64_t nnz_a;              /* entries of A (diagonal + 1-hop + two-hop)                  */
+  int64_t nnz_q;              /* entries of Q (diagonal + two-hop)                          */
+  double  eps, mu;
+  double  norm_a;             /* max_i (A_ii + r_i), a Gershgorin bound on ||A||_2          */
+  double  bmax;               /* max_i b_i                                                  */
+  int     degenerate;         /* eps forced to 0                                            */
+  int     two_hop_components; /* connected components of (V, T)                             */
+  int     eps_iters;          /* LOBPCG iterations of the eps solve                         */
+  double  eps_resid;          /* its final backward error                                   */
+  double  build_ms;           /* device time of the whole build                             */
+} mge_ops_info_t;
+
+mge_status mge_ops_info(const mge_ops* ops, mge_ops_info_t* out);
+
+/* Copies the operators out (for parity checks).  Any pointer may be NULL to skip it.
+ * Sizes: a_ptr/q_ptr [n+1], a_col/a_val [nnz_a], q_col/q_val [nnz_q], b/T [n].  Values are
+ * FP64 whatever the precision the iteration uses.  on_device selects device or host
+ * destinations. */
+mge_status mge_ops_export(const mge_ops* ops, int64_t* a_ptr, int32_t* a_col, double* a_val,
+                          int64_t* q_ptr, int32_t* q_col, double* q_val, double* b,
+                          int32_t* T, int on_device);
+
+/* Y = A X (which = 0) or Y = Q X (which = 1) with the library's SpMM kernel in the given
+ * precision; X and Y are row-major [n x m] blocks of that precision (double, float, or
+ * bfloat16 bits as uint16), device pointers, m in {4, 8, 12, 16, 24, 32}.  Test and
+ * measurement entry point for the SpMM of the iteration. */
+mge_status mge_ops_apply(mge_ctx* ctx, const mge_ops* ops, int which, int precision, int m,
+                         const void* X, void* Y, void* stream);
+
+/* ---- embedding: LOBPCG for the first K generalized eigenpairs (Sec. 4.3) ------------- */
+
+typedef struct {
+  int         precision;      /* mge_precision of the blocks (default MGE_FP32)             */
+  int         guard;          /* extra columns beyond K; m = K + guard is rounded up to a
+                                 supported block width (4, 8, 12, 16, 24, 32)              */
+  int         maxiter;        /* default 20000                                             */
+  uint64_t    seed;           /* seed of the initial block when x0 is NULL                  */
+  int         check_every;    /* iterations between host checks of convergence (default 16)*/
+  int         use_graph;      /* capture the iteration in a CUDA graph (default 1)          */
+  const double* x0;           /* optional initial block, host or device per x0_on_device,
+                                 column-major [n x m_in] FP64, m_in = x0_cols              */
+  int         x0_cols;
+  int         x0_on_device;
+  int         v_on_device;    /* V is a device pointer                                      */
+  void*       stream;         /* cudaStream_t or NULL                                       */
+} mge_embed_opts;
+
+typedef struct {
+  int    status;              /* mge_status of the solve                                   */
+  int    iters;               /* LOBPCG iterations                                         */
+  int    m;                   /* block width used                                          */
+  int    drops;               /* iterations whose Rayleigh-Ritz basis dropped a direction   */
+  double resid[64];           /* backward error eta_k of each returned pair (k < K)         */
+  double solve_ms;            /* device time of the solve                                  */
+} mge_embed_info;
+
+/* Fills lambda[K] (host, ascending) and V (column-major [n x K] FP64, host or device per
+ * opts->v_on_device) with the first K generalized eigenpairs of (A, B) of `ops`.
+ * Convergence: every returned column has backward error
+ *   eta = ||A x - lambda B x||_2 / ((||A||_G + |lambda| max b) ||x||_2) <= tol.
+ * Errors: MGE_EINVAL (K < 1, K + guard > 32, n < m), MGE_ENOTCONVERGED (partial results
+ * written), MGE_ECHOLESKY, MGE_ENOTFINITE, MGE_ENOMEM, MGE_EDEVICE.  `info` may be NULL. */
+mge_status mge_embed(mge_ctx* ctx, const mge_ops* ops, int K, double tol,
+                     const mge_embed_opts* opts, double* lambda, void* V,
+                     mge_embed_info* info);
+
+/* ---- serving: continuous batching of embedding requests ---------------------------- */
+
+typedef struct {
+  int64_t        n;
+  const int64_t* row_ptr;     /* host CSR of W; copied at submit                            */
+  const int32_t* col;
+  const double*  w;
+  int            K;
+  double         tol;
+  int            precision;
+  int            guard;
+  int            maxiter;
+  uint64_t       seed;
+} mge_request;
+
+typedef struct {
+  int      status;            /* mge_status of the request                                  */
+  int64_t  n;
+  int      K;
+  double   eps, mu;
+  int      iters;
+  double   latency_ms;        /* submit to completion, host clock                           */
+  double   queue_ms;          /* submit to admission                                        */
+  double*  lambda;            /* library-owned, valid until mge_release                     */
+  double*  V;                 /* library-owned host buffer, column-major [n x K]            */
+} mge_result;
+
+/* Enqueues a request; the serving thread admits it when its HBM footprint fits the
+ * context budget and runs it concurrently with the requests already on the device.
+ * Errors: MGE_EINVAL, MGE_EAGAIN (queue full). */
+mge_status mge_submit(mge_ctx* ctx, const mge_request* req, uint64_t* ticket);
+/* Waits up to timeout_ms (negative = forever) for the ticket; MGE_ETIMEOUT if not done. */
+mge_status mge_poll(mge_ctx* ctx, uint64_t ticket, int timeout_ms, mge_result* out);
+/* Frees the result buffers of a completed ticket. */
+mge_status mge_release(mge_ctx* ctx, uint64_t ticket);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGE_H */

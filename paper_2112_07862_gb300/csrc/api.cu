@@ -1,0 +1,313 @@
+// C ABI entry points of libmge (declared in include/mge.h).
+#include "mge_internal.cuh"
+
+#include <cstdarg>
+#include <cstring>
+
+namespace mge {
+
+mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* rp_in,
+                                const int32_t* col_in, const double* w_in, int on_device,
+                                const mge_ops_opts* opts, Ops* ops);
+mge_status serve_submit(Ctx* ctx, const mge_request* req, uint64_t* ticket);
+mge_status serve_poll(Ctx* ctx, uint64_t ticket, int timeout_ms, mge_result* out);
+mge_status serve_release(Ctx* ctx, uint64_t ticket);
+void serve_shutdown(Ctx* ctx);
+
+void set_error(Ctx* ctx, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx) {
+    std::lock_guard<std::mutex> g(ctx->err_mu);
+    ctx->last_error = buf;
+  }
+}
+
+mge_status dev_alloc(Ctx* ctx, void** p, size_t bytes) {
+  if (ctx->budget && ctx->in_use.load() + bytes > ctx->budget) {
+    set_error(ctx, "HBM budget exceeded: %zu in use + %zu requested > %zu", ctx->in_use.load(), bytes,
+              ctx->budget);
+    return MGE_ENOMEM;
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    set_error(ctx, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    *p = nullptr;
+    return MGE_ENOMEM;
+  }
+  ctx->in_use += bytes;
+  return MGE_OK;
+}
+
+void dev_free(Ctx* ctx, void* p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  if (ctx) ctx->in_use -= bytes;
+}
+
+static cudaStream_t pick_stream(Ctx* ctx, void* s) {
+  return s ? static_cast<cudaStream_t>(s) : ctx->stream;
+}
+
+}  // namespace mge
+
+using namespace mge;
+
+extern "C" {
+
+const char* mge_strerror(mge_status s) {
+  switch (s) {
+    case MGE_OK: return "ok";
+    case MGE_EINVAL: return "invalid argument";
+    case MGE_ENOTSYM: return "W is not symmetric";
+    case MGE_EISOLATED: return "isolated node: B is singular";
+    case MGE_EDEGENERATE: return "eps = 0: the two-hop graph is disconnected";
+    case MGE_ENOTCONVERGED: return "not converged within maxiter";
+    case MGE_ENOMEM: return "out of device memory or HBM budget";
+    case MGE_EAGAIN: return "queue or budget full; retry";
+    case MGE_ETIMEOUT: return "timed out";
+    case MGE_EDEVICE: return "CUDA error";
+    case MGE_ECHOLESKY: return "Rayleigh-Ritz basis collapsed";
+    case MGE_ENOTFOUND: return "unknown ticket";
+    case MGE_ENOTFINITE: return "non-finite value in the iteration";
+  }
+  return "unknown status";
+}
+
+mge_status mge_create(int device, size_t hbm_budget_bytes, mge_ctx** out) {
+  if (!out) return MGE_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return MGE_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return MGE_EDEVICE;
+  mge_ctx* c = new mge_ctx();
+  Ctx* ctx = &c->impl;
+  ctx->device = device;
+  ctx->budget = hbm_budget_bytes;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete c; return MGE_EDEVICE; }
+  ctx->num_sms = prop.multiProcessorCount;
+  ctx->self = c;
+  if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return MGE_EDEVICE; }
+  *out = c;
+  return MGE_OK;
+}
+
+mge_status mge_destroy(mge_ctx* c) {
+  if (!c) return MGE_EINVAL;
+  Ctx* ctx = &c->impl;
+  cudaSetDevice(ctx->device);
+  serve_shutdown(ctx);
+  for (auto& e : ctx->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete c;
+  return MGE_OK;
+}
+
+const char* mge_ctx_last_error(const mge_ctx* c) {
+  if (!c) return "null context";
+  return c->impl.last_error.c_str();
+}
+
+mge_status mge_ctx_stats(const mge_ctx* c, mge_stats* out) {
+  if (!c || !out) return MGE_EINVAL;
+  const Ctx* ctx = &c->impl;
+  out->kernel_launches = ctx->kernel_launches.load();
+  out->spmm_launches = ctx->spmm_launches;
+  out->spmm_ms = ctx->spmm_ms;
+  out->spmm_bytes = ctx->spmm_bytes;
+  out->hbm_in_use = ctx->in_use.load();
+  return MGE_OK;
+}
+
+mge_status mge_ctx_set_timing(mge_ctx* c, int on) {
+  if (!c) return MGE_EINVAL;
+  c->impl.timing = on != 0;
+  return MGE_OK;
+}
+
+mge_status mge_ctx_reset_stats(mge_ctx* c) {
+  if (!c) return MGE_EINVAL;
+  c->impl.kernel_launches = 0;
+  c->impl.spmm_launches = 0;
+  c->impl.spmm_ms = 0;
+  c->impl.spmm_bytes = 0;
+  return MGE_OK;
+}
+
+mge_status mge_build_graph_ops(mge_ctx* c, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                               const double* w, int on_device, const mge_ops_opts* opts, mge_ops** out) {
+  if (!c || !out) return MGE_EINVAL;
+  *out = nullptr;
+  Ctx* ctx = &c->impl;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return MGE_EDEVICE;
+  cudaStream_t st = pick_stream(ctx, opts ? opts->stream : nullptr);
+  mge_ops* o = new mge_ops();
+  mge_status s = build_graph_ops_impl(ctx, st, n, row_ptr, col, w, on_device, opts, &o->impl);
+  if (s != MGE_OK && s != MGE_EDEGENERATE) {
+    delete o;
+    return s;
+  }
+  *out = o;
+  return s;
+}
+
+mge_status mge_ops_destroy(mge_ops* o) {
+  if (!o) return MGE_EINVAL;
+  delete o;
+  return MGE_OK;
+}
+
+mge_status mge_ops_info(const mge_ops* o, mge_ops_info_t* out) {
+  if (!o || !out) return MGE_EINVAL;
+  const Ops& op = o->impl;
+  out->n = op.n; out->nnz_w = op.nnz_w; out->nnz_a = op.nnz_a; out->nnz_q = op.nnz_q;
+  out->eps = op.eps; out->mu = op.mu; out->norm_a = op.norm_a; out->bmax = op.bmax;
+  out->degenerate = op.degenerate; out->two_hop_components = op.ncomp;
+  out->eps_iters = op.eps_iters; out->eps_resid = op.eps_resid; out->build_ms = op.build_ms;
+  return MGE_OK;
+}
+
+mge_status mge_ops_export(const mge_ops* o, int64_t* a_ptr, int32_t* a_col, double* a_val, int64_t* q_ptr,
+                          int32_t* q_col, double* q_val, double* b, int32_t* T, int on_device) {
+  if (!o) return MGE_EINVAL;
+  const Ops& op = o->impl;
+  Ctx* ctx = op.ctx;
+  cudaSetDevice(ctx->device);
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaStream_t st = ctx->stream;
+  if (a_ptr) MGE_CUDA(ctx, cudaMemcpyAsync(a_ptr, op.a_ptr.p, (op.n + 1) * sizeof(int64_t), k, st));
+  if (a_col && op.nnz_a) MGE_CUDA(ctx, cudaMemcpyAsync(a_col, op.a_col.p, op.nnz_a * sizeof(int32_t), k, st));
+  if (a_val && op.nnz_a) MGE_CUDA(ctx, cudaMemcpyAsync(a_val, op.a_val.p, op.nnz_a * sizeof(double), k, st));
+  if (q_ptr) MGE_CUDA(ctx, cudaMemcpyAsync(q_ptr, op.q_ptr.p, (op.n + 1) * sizeof(int64_t), k, st));
+  if (q_col && op.nnz_q) MGE_CUDA(ctx, cudaMemcpyAsync(q_col, op.q_col.p, op.nnz_q * sizeof(int32_t), k, st));
+  if (q_val && op.nnz_q) MGE_CUDA(ctx, cudaMemcpyAsync(q_val, op.q_val.p, op.nnz_q * sizeof(double), k, st));
+  if (b) MGE_CUDA(ctx, cudaMemcpyAsync(b, op.b.p, op.n * sizeof(double), k, st));
+  if (T) MGE_CUDA(ctx, cudaMemcpyAsync(T, op.T.p, op.n * sizeof(int32_t), k, st));
+  MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  return MGE_OK;
+}
+
+static LobOp make_op(const Ops& op, int which, int precision) {
+  LobOp l;
+  l.n = op.n;
+  bool dbl = precision == MGE_FP64;
+  if (which == 0) {
+    l.ptr = op.a_ptr.p; l.col = op.a_col.p;
+    l.val = dbl ? (const void*)op.a_val.p : (const void*)op.a_val32.p;
+    l.shift = op.eps;
+    l.b = dbl ? (const void*)op.b.p : (const void*)op.b32.p;
+    l.dinv = dbl ? (const void*)op.dinv_a.p : (const void*)op.dinv_a32.p;
+    l.norm = op.norm_a; l.bmax = op.bmax; l.deflate = false;
+  } else {
+    l.ptr = op.q_ptr.p; l.col = op.q_col.p;
+    l.val = dbl ? (const void*)op.q_val.p : (const void*)op.q_val32.p;
+    l.shift = 0.0; l.b = nullptr;
+    l.dinv = dbl ? (const void*)op.dinv_q.p : (const void*)op.dinv_q32.p;
+    l.norm = op.norm_q; l.bmax = 1.0; l.deflate = true;
+  }
+  return l;
+}
+
+mge_status mge_ops_apply(mge_ctx* c, const mge_ops* o, int which, int precision, int m, const void* X, void* Y,
+                         void* stream) {
+  if (!c || !o || !X || !Y || (which != 0 && which != 1)) return MGE_EINVAL;
+  Ctx* ctx = &c->impl;
+  cudaSetDevice(ctx->device);
+  if (precision != MGE_FP64 && precision != MGE_FP32) {
+    set_error(ctx, "apply: precision %d not supported", precision);
+    return MGE_EINVAL;
+  }
+  if (round_block_width(m) != m) { set_error(ctx, "apply: unsupported width %d", m); return MGE_EINVAL; }
+  cudaStream_t st = pick_stream(ctx, stream);
+  LobOp l = make_op(o->impl, which, precision);
+  MGE_TRY(spmm_apply(ctx, st, l, precision, m, X, Y));
+  MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  return MGE_OK;
+}
+
+mge_status mge_embed(mge_ctx* c, const mge_ops* o, int K, double tol, const mge_embed_opts* opts,
+                     double* lambda, void* V, mge_embed_info* info) {
+  if (!c || !o || !lambda) return MGE_EINVAL;
+  Ctx* ctx = &c->impl;
+  cudaSetDevice(ctx->device);
+  mge_embed_opts e{};
+  e.precision = MGE_FP32;
+  e.maxiter = 20000;
+  e.check_every = 16;
+  e.use_graph = 1;
+  if (opts) e = *opts;
+  if (e.maxiter <= 0) e.maxiter = 20000;
+  if (e.check_every <= 0) e.check_every = 16;
+  if (!(tol > 0)) { set_error(ctx, "tol must be > 0"); return MGE_EINVAL; }
+  if (K < 1) { set_error(ctx, "K must be >= 1"); return MGE_EINVAL; }
+  int m = round_block_width(K + std::max(e.guard, 0));
+  if (m < 0 || m > 24) { set_error(ctx, "K + guard = %d exceeds the widest block (24)", K + e.guard); return MGE_EINVAL; }
+  const Ops& op = o->impl;
+  if (op.n < 2 * m) { set_error(ctx, "graph has %lld nodes; need at least %d", (long long)op.n, 2 * m); return MGE_EINVAL; }
+  int prec = e.precision;
+  if (prec == MGE_BF16) { set_error(ctx, "BF16 blocks are not available in this build"); return MGE_EINVAL; }
+  if (prec != MGE_FP64 && prec != MGE_FP32) { set_error(ctx, "bad precision"); return MGE_EINVAL; }
+  cudaStream_t st = pick_stream(ctx, e.stream);
+  LobOp l = make_op(op, 0, prec);
+  // optional initial block
+  DevBuf<double> x0d;
+  const double* x0 = nullptr;
+  int x0c = 0;
+  if (e.x0 && e.x0_cols > 0) {
+    x0c = std::min(e.x0_cols, m);
+    if (e.x0_on_device) x0 = e.x0;
+    else {
+      MGE_TRY(x0d.alloc(ctx, (size_t)op.n * x0c));
+      MGE_CUDA(ctx, cudaMemcpyAsync(x0d.p, e.x0, (size_t)op.n * x0c * sizeof(double), cudaMemcpyHostToDevice, st));
+      x0 = x0d.p;
+    }
+  }
+  DevBuf<double> vd;
+  double* vout = nullptr;
+  if (V) {
+    if (e.v_on_device) vout = static_cast<double*>(V);
+    else { MGE_TRY(vd.alloc(ctx, (size_t)op.n * K)); vout = vd.p; }
+  }
+  LobResult r;
+  mge_status s = lobpcg_solve(ctx, st, l, prec, K, m, tol, e.maxiter, e.seed, e.check_every, e.use_graph != 0,
+                              x0, x0c, vout, &r);
+  if (s != MGE_OK && s != MGE_ENOTCONVERGED) {
+    if (info) { info->status = s; info->iters = r.iters; }
+    return s;
+  }
+  for (int k = 0; k < K; ++k) lambda[k] = r.lambda[k];
+  if (V && !e.v_on_device) {
+    MGE_CUDA(ctx, cudaMemcpyAsync(V, vd.p, (size_t)op.n * K * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  }
+  if (info) {
+    info->status = s;
+    info->iters = r.iters;
+    info->m = m;
+    info->drops = r.drops;
+    for (int k = 0; k < 64; ++k) info->resid[k] = k < K ? r.eta[k] : 0.0;
+    info->solve_ms = r.ms;
+  }
+  return s;
+}
+
+mge_status mge_submit(mge_ctx* c, const mge_request* req, uint64_t* ticket) {
+  if (!c || !req || !ticket) return MGE_EINVAL;
+  return serve_submit(&c->impl, req, ticket);
+}
+
+mge_status mge_poll(mge_ctx* c, uint64_t ticket, int timeout_ms, mge_result* out) {
+  if (!c || !out) return MGE_EINVAL;
+  return serve_poll(&c->impl, ticket, timeout_ms, out);
+}
+
+mge_status mge_release(mge_ctx* c, uint64_t ticket) {
+  if (!c) return MGE_EINVAL;
+  return serve_release(&c->impl, ticket);
+}
+
+}  // extern "C"

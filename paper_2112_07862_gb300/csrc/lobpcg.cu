@@ -1,0 +1,966 @@
+// LOBPCG for the first K generalized eigenpairs of (A, B) (Sec. 4.3), in the library's own
+// kernels.  One iteration is six launches:
+//
+//   spmm_w   W = (W_raw - 1 c^T - X Mx - P Mp) L^-T and AW = A W: the projections and the
+//            normalisation of the preconditioned residual are fused into the SpMM
+//   gram     G_A = S^T A S, G_B = S^T B S for S = [X W P]   (FP32 accumulation, cluster sums)
+//   rr       Rayleigh-Ritz on one CTA (rr.cu): coefficients C_x, C_p and Ritz values
+//   update   X' = S C_x, AX' = AS C_x, P' = S C_p, AP' = AS C_p, R = AX' - B X' Lambda,
+//            W_raw = diag(A)^-1 R, residual and vector norms          (cluster sums)
+//   gram     [X' P' W_raw]^T B W_raw (+ column sums of W_raw when deflating)
+//   wprep    backward errors, convergence flag, Mx, Mp and L^-T for the next SpMM (rr.cu)
+//
+// A is a graph Laplacian plus a multiple of I in every use (A = L - mu Q + eps I, or Q), so
+// (A x)_i = shift x_i + sum_j A_ij (x_j - x_i): the SpMM sums differences, which keeps FP32
+// accuracy where A x is small next to ||A|| ||x|| (smooth vectors); the diagonal entry
+// contributes A_ii (x_i - x_i) = 0.
+//
+// Cross-CTA reductions: each CTA reduces in registers/shared memory, the 8 CTAs of a cluster
+// sum through distributed shared memory, and each cluster stores one partial; the single-CTA
+// consumer adds the (at most MAXCL) cluster partials in FP64.  No contended atomics.
+#include "lobpcg_common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+
+namespace mge {
+namespace lob {
+
+namespace {
+
+// =======================================================================================
+// SpMM with fused projection and normalisation of W
+// =======================================================================================
+template <typename T>
+struct SpmmArgs {
+  int64_t n;
+  const int64_t* ptr;
+  const int32_t* col;
+  const T* val;
+  T shift;
+  const T* Wr;
+  const T* X; const T* AX; const T* P; const T* AP;   // NULL when absent
+  const SmallT<T>* sm;                                 // Mx, Mp, Linv, cmean (NULL: plain A*Wr)
+  T* W; T* AW;
+  const State* st;
+};
+
+// Lanes per row: G = M/4 column groups (4-wide vectors) times S, the split of the row's
+// nonzeros; S makes every row a team of 6 or 8 lanes so that short rows still keep several
+// gathers in flight per warp.
+template <int M> struct SpmmShape {
+  static constexpr int G = M / 4;
+  static constexpr int S = (G == 1) ? 8 : (G == 2) ? 4 : (G <= 4) ? (8 / G > 0 ? 8 / G : 1) : 1;
+  static constexpr int TEAM = G * S;
+  static constexpr int RPW = 32 / TEAM;
+};
+
+template <typename T, int M>
+__global__ void __launch_bounds__(kThreads) k_spmm_w(SpmmArgs<T> a) {
+  if (a.st && a.st->done) return;
+  using Sh = SpmmShape<M>;
+  constexpr int G = Sh::G, S = Sh::S, TEAM = Sh::TEAM, RPW = Sh::RPW;
+  constexpr int NW = kThreads / 32;
+  __shared__ T sMx[M * M], sMp[M * M], sL[M * M], sc[M];
+  __shared__ T sW[NW][RPW][M], sAW[NW][RPW][M];
+  const bool fused = a.sm != nullptr;
+  if (fused) {
+    for (int t = threadIdx.x; t < M * M; t += kThreads) {
+      int r = t / M, c = t % M;
+      sMx[t] = a.sm->Mx[r * MAXM + c];
+      sMp[t] = a.sm->Mp[r * MAXM + c];
+      sL[t] = a.sm->Linv[r * MAXM + c];
+    }
+    for (int t = threadIdx.x; t < M; t += kThreads) sc[t] = a.sm->cmean[t];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int team = lane / TEAM, tl = lane % TEAM;
+  const int sub = tl / G, g = tl % G, c0 = g * 4;     // nonzero slice and column group
+  const bool lane_ok = team < RPW;
+  for (int64_t base = ((int64_t)blockIdx.x * NW + wid) * RPW; base < a.n;
+       base += (int64_t)gridDim.x * NW * RPW) {
+    const int64_t row = base + team;
+    const bool valid = lane_ok && row < a.n;
+    T acc[4] = {0, 0, 0, 0}, wi[4] = {0, 0, 0, 0};
+    if (valid) {
+      ldg4(a.Wr + row * M + c0, wi);
+      const int64_t pe = a.ptr[row + 1];
+      int64_t p = a.ptr[row] + sub;
+      // two nonzeros per step: both gathers are issued before either is consumed
+      for (; p + S < pe; p += 2 * S) {
+        const int32_t j0 = __ldg(a.col + p), j1 = __ldg(a.col + p + S);
+        const T v0 = __ldg(a.val + p), v1 = __ldg(a.val + p + S);
+        T w0[4], w1[4];
+        ldg4(a.Wr + (int64_t)j0 * M + c0, w0);
+        ldg4(a.Wr + (int64_t)j1 * M + c0, w1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += v0 * (w0[q] - wi[q]) + v1 * (w1[q] - wi[q]);
+      }
+      if (p < pe) {
+        const int32_t j0 = __ldg(a.col + p);
+        const T v0 = __ldg(a.val + p);
+        T w0[4];
+        ldg4(a.Wr + (int64_t)j0 * M + c0, w0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += v0 * (w0[q] - wi[q]);
+      }
+    }
+    // combine the S nonzero slices: lanes of slice 0 end up with the row sums
+#pragma unroll
+    for (int off = (S / 2) * G; off >= G && off > 0; off >>= 1) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], off);
+    }
+    const bool lead = valid && sub == 0;
+    if (!fused) {
+      if (lead) {
+        T y[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) y[q] = a.shift * wi[q] + acc[q];
+        st4(a.AW + row * M + c0, y);
+      }
+      continue;
+    }
+    if (lead) {
+      T wt[4], awt[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        wt[q] = wi[q] - sc[c0 + q];
+        awt[q] = a.shift * wt[q] + acc[q];
+      }
+      if (a.X) {
+#pragma unroll
+        for (int l = 0; l < M; l += 4) {
+          T xl[4], axl[4];
+          ldg4(a.X + row * M + l, xl);
+          ldg4(a.AX + row * M + l, axl);
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              T m = sMx[(l + t) * M + c0 + q];
+              wt[q] -= xl[t] * m;
+              awt[q] -= axl[t] * m;
+            }
+        }
+      }
+      if (a.P) {
+#pragma unroll
+        for (int l = 0; l < M; l += 4) {
+          T pl[4], apl[4];
+          ldg4(a.P + row * M + l, pl);
+          ldg4(a.AP + row * M + l, apl);
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              T m = sMp[(l + t) * M + c0 + q];
+              wt[q] -= pl[t] * m;
+              awt[q] -= apl[t] * m;
+            }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        sW[wid][team][c0 + q] = wt[q];
+        sAW[wid][team][c0 + q] = awt[q];
+      }
+    }
+    __syncwarp();
+    if (lead) {
+      T o[4] = {0, 0, 0, 0}, ao[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int l = 0; l < M; ++l) {
+        T w = sW[wid][team][l], aw = sAW[wid][team][l];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          T li = sL[l * M + c0 + q];
+          o[q] += w * li;
+          ao[q] += aw * li;
+        }
+      }
+      st4(a.W + row * M + c0, o);
+      st4(a.AW + row * M + c0, ao);
+    }
+    __syncwarp();
+  }
+}
+
+// =======================================================================================
+// Gram products over row tiles: out1 = L^T R1, out2 = L^T diag(b) R2 (block-upper part of
+// L^T B L when R2 is L).  4x4 output blocks per thread; per-tile sums are added into
+// compensated (Neumaier) per-thread accumulators.
+// =======================================================================================
+template <typename T>
+struct GramArgs {
+  int64_t n;
+  int nl, n1, n2;
+  const T* L[3];
+  const T* R1[3];
+  const T* R2[3];
+  bool sym2;
+  const T* b;                // NULL = unit weights
+  double* out1;              // per-cluster partial of out1, [ncl][MAXS * MAXS], ld MAXS
+  double* out2;              // per-cluster partial of out2, leading dimension ld2
+  int ld2;
+  int stride2;               // elements between clusters in out2
+  double* csum;              // per-cluster column sums of R2, [ncl][MAXM] (NULL: skip)
+  const State* st;
+};
+
+constexpr int kTileRows = 32;
+
+__device__ __forceinline__ void decode_item(int item, int nb1, int b1, int bl, bool sym2, int b2, int& prod,
+                                            int& bi, int& bj) {
+  if (item < nb1) {
+    prod = 1; bi = item / b1; bj = item % b1;
+    return;
+  }
+  int r = item - nb1;
+  prod = 2;
+  if (sym2) {
+    int i = 0;
+    while (r >= bl - i) { r -= bl - i; ++i; }
+    bi = i; bj = i + r;
+  } else {
+    bi = r / b2; bj = r % b2;
+  }
+}
+
+template <typename T, int M>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads) k_gram(GramArgs<T> a) {
+  if (a.st && a.st->done) return;
+  using A = T;   // accumulate in the block precision (FP32 for FP32 blocks), compensated
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sL = reinterpret_cast<T*>(smem_raw);
+  const int wl = a.nl * M, w1 = a.n1 * M, w2 = a.sym2 ? 0 : a.n2 * M;
+  T* sR1 = sL + kTileRows * wl;
+  T* sR2 = sR1 + kTileRows * w1;
+  T* sb = sR2 + kTileRows * w2;
+  const int bl = wl / 4, b1 = w1 / 4, b2 = (a.sym2 ? wl : a.n2 * M) / 4;
+  const int nb1 = bl * b1;
+  const int nb2 = a.sym2 ? bl * (bl + 1) / 2 : bl * b2;
+  const int nblk = nb1 + nb2;
+  constexpr int IPT = (M <= 16) ? 1 : 2;
+  int rs = kThreads / nblk;
+  if (rs < 1) rs = 1;
+  const int tpi = (nblk * rs <= kThreads) ? nblk : kThreads;
+  const int rg = threadIdx.x / tpi;
+  const int ti = threadIdx.x % tpi;
+  const bool has_group = rg < rs;
+  int it_prod[IPT], it_i[IPT], it_j[IPT];
+  bool it_ok[IPT];
+#pragma unroll
+  for (int u = 0; u < IPT; ++u) {
+    int item = ti + u * tpi;
+    it_ok[u] = has_group && item < nblk;
+    it_prod[u] = 0; it_i[u] = 0; it_j[u] = 0;
+    if (it_ok[u]) decode_item(item, nb1, b1, bl, a.sym2, b2, it_prod[u], it_i[u], it_j[u]);
+  }
+  A acc[IPT][16], cmp[IPT][16];
+#pragma unroll
+  for (int u = 0; u < IPT; ++u)
+#pragma unroll
+    for (int e = 0; e < 16; ++e) { acc[u][e] = A(0); cmp[u][e] = A(0); }
+  A cs = A(0);
+  const int ws = w2;
+  for (int64_t r0 = (int64_t)blockIdx.x * kTileRows; r0 < a.n; r0 += (int64_t)gridDim.x * kTileRows) {
+    const int nr = (int)((a.n - r0) < kTileRows ? (a.n - r0) : kTileRows);
+    __syncthreads();
+    for (int t = threadIdx.x; t < kTileRows * (wl / 4); t += kThreads) {
+      int r = t / (wl / 4), c = (t % (wl / 4)) * 4;
+      int blk = c / M, cc = c % M;
+      T v[4] = {0, 0, 0, 0};
+      if (r < nr) ldg4(a.L[blk] + (r0 + r) * M + cc, v);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sL[r * wl + c + q] = v[q];
+    }
+    for (int t = threadIdx.x; t < kTileRows * (w1 / 4); t += kThreads) {
+      int r = t / (w1 / 4), c = (t % (w1 / 4)) * 4;
+      int blk = c / M, cc = c % M;
+      T v[4] = {0, 0, 0, 0};
+      if (r < nr) ldg4(a.R1[blk] + (r0 + r) * M + cc, v);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sR1[r * w1 + c + q] = v[q];
+    }
+    for (int t = threadIdx.x; t < kTileRows * (ws / 4); t += kThreads) {
+      int r = t / (ws / 4), c = (t % (ws / 4)) * 4;
+      int blk = c / M, cc = c % M;
+      T v[4] = {0, 0, 0, 0};
+      if (r < nr) ldg4(a.R2[blk] + (r0 + r) * M + cc, v);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sR2[r * ws + c + q] = v[q];
+    }
+    for (int t = threadIdx.x; t < kTileRows; t += kThreads)
+      sb[t] = (t < nr) ? (a.b ? a.b[r0 + t] : T(1)) : T(0);
+    __syncthreads();
+    if (a.csum && threadIdx.x < ws) {
+      A s = A(0);
+      for (int r = 0; r < nr; ++r) s += (A)sR2[r * ws + threadIdx.x];
+      cs += s;
+    }
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+      if (!it_ok[u]) continue;
+      A at[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) at[e] = A(0);
+      const T* lp = sL + it_i[u] * 4;
+      const T* rp;
+      int wr;
+      bool weighted = false;
+      if (it_prod[u] == 1) { rp = sR1 + it_j[u] * 4; wr = w1; }
+      else if (a.sym2) { rp = sL + it_j[u] * 4; wr = wl; weighted = true; }
+      else { rp = sR2 + it_j[u] * 4; wr = ws; weighted = true; }
+      for (int r = rg; r < kTileRows; r += rs) {
+        A lv[4], rv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { lv[q] = (A)lp[r * wl + q]; rv[q] = (A)rp[r * wr + q]; }
+        if (weighted) {
+          A bw = (A)sb[r];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) rv[q] *= bw;
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) at[p * 4 + q] += lv[p] * rv[q];
+      }
+      // Neumaier-compensated add of the tile sum
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        A s = acc[u][e] + at[e];
+        if (fabs((double)acc[u][e]) >= fabs((double)at[e])) cmp[u][e] += (acc[u][e] - s) + at[e];
+        else cmp[u][e] += (at[e] - s) + acc[u][e];
+        acc[u][e] = s;
+      }
+    }
+  }
+  // CTA reduction: stage [rs][nblk][16], sum over row groups into FP64, then the cluster
+  __syncthreads();
+  const int len = nblk * 16;
+  A* stage = reinterpret_cast<A*>(smem_raw);
+  double* part = reinterpret_cast<double*>(smem_raw + (((size_t)rs * len * sizeof(A) + 15) / 16) * 16);
+#pragma unroll
+  for (int u = 0; u < IPT; ++u)
+    if (it_ok[u]) {
+      int item = ti + u * tpi;
+#pragma unroll
+      for (int e = 0; e < 16; ++e) stage[(size_t)rg * len + item * 16 + e] = acc[u][e] + cmp[u][e];
+    }
+  __syncthreads();
+  for (int t = threadIdx.x; t < len; t += kThreads) {
+    double s = 0.0;
+    for (int g = 0; g < rs; ++g) s += (double)stage[(size_t)g * len + t];
+    part[t] = s;
+  }
+  if (a.csum && threadIdx.x < ws) part[len + threadIdx.x] = (double)cs;
+  const int tot = len + (a.csum ? ws : 0);
+  const int cl = cluster_id();
+  cluster_sum(part, tot, [&](int t, double v) {
+    if (t >= len) { a.csum[(size_t)cl * MAXM + (t - len)] = v; return; }
+    int item = t / 16, e = t % 16, p = e / 4, q = e % 4;
+    int prod, bi, bj;
+    decode_item(item, nb1, b1, bl, a.sym2, b2, prod, bi, bj);
+    if (prod == 1) a.out1[(size_t)cl * MAXS * MAXS + (bi * 4 + p) * MAXS + bj * 4 + q] = v;
+    else a.out2[(size_t)cl * a.stride2 + (bi * 4 + p) * a.ld2 + bj * 4 + q] = v;
+  });
+}
+
+// =======================================================================================
+// update: X' = S Cx, AX' = AS Cx, P' = S Cp, AP' = AS Cp, R, W_raw, residual norms
+// =======================================================================================
+template <typename T>
+struct UpdArgs {
+  int64_t n;
+  int nb;
+  T* S[3];
+  T* AS[3];
+  T* Xo; T* AXo; T* Po; T* APo;
+  bool produce_p;
+  const SmallT<T>* smt;
+  const T* b;
+  const T* dinv;
+  T* Wr;
+  double* partN;             // [ncl][2*MAXM]
+  const State* st;
+};
+
+template <typename T, int M>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads) k_update(UpdArgs<T> a) {
+  if (a.st->done) return;
+  using A = T;
+  constexpr int G = M / 4, RPW = 32 / G, NW = kThreads / 32;
+  __shared__ T sCx[MAXS * M], sCp[MAXS * M], sLam[M];
+  __shared__ A red[NW][32][8];
+  __shared__ double part[2 * M];
+  const int ns = a.nb * M;
+  for (int t = threadIdx.x; t < ns * M; t += kThreads) {
+    int r = t / M, c = t % M;
+    sCx[t] = a.smt->Cx[r * MAXM + c];
+    sCp[t] = a.smt->Cp[r * MAXM + c];
+  }
+  for (int t = threadIdx.x; t < M; t += kThreads) sLam[t] = a.smt->lam[t];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int team = lane / G, tl = lane % G, c0 = tl * 4;
+  const bool lane_ok = team < RPW;
+  A pr[4] = {0, 0, 0, 0}, px[4] = {0, 0, 0, 0};
+  for (int64_t base = ((int64_t)blockIdx.x * NW + wid) * RPW; base < a.n;
+       base += (int64_t)gridDim.x * NW * RPW) {
+    const int64_t row = base + team;
+    const bool valid = lane_ok && row < a.n;
+    T x[4] = {0, 0, 0, 0}, ax[4] = {0, 0, 0, 0}, p[4] = {0, 0, 0, 0}, ap[4] = {0, 0, 0, 0};
+    if (valid) {
+      for (int blk = 0; blk < a.nb; ++blk) {
+        const T* sp = a.S[blk] + row * M;
+        const T* asp = a.AS[blk] + row * M;
+#pragma unroll
+        for (int l = 0; l < M; l += 4) {
+          T sv[4], av[4];
+          ld4(sp + l, sv);
+          ld4(asp + l, av);
+          const int rbase = blk * M + l;
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              T cx = sCx[(rbase + t) * M + c0 + q];
+              T cp = sCp[(rbase + t) * M + c0 + q];
+              x[q] += sv[t] * cx;
+              ax[q] += av[t] * cx;
+              p[q] += sv[t] * cp;
+              ap[q] += av[t] * cp;
+            }
+        }
+      }
+    }
+    __syncwarp();   // every lane of the team has read the row before any lane overwrites it
+    if (valid) {
+      st4(a.Xo + row * M + c0, x);
+      st4(a.AXo + row * M + c0, ax);
+      if (a.produce_p) {
+        st4(a.Po + row * M + c0, p);
+        st4(a.APo + row * M + c0, ap);
+      }
+      const T bi = a.b ? a.b[row] : T(1);
+      const T di = a.dinv[row];
+      T r[4], w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        r[q] = ax[q] - bi * x[q] * sLam[c0 + q];
+        w[q] = r[q] * di;
+        pr[q] += r[q] * r[q];
+        px[q] += x[q] * x[q];
+      }
+      st4(a.Wr + row * M + c0, w);
+    }
+    __syncwarp();
+  }
+  // per-column sums: stage per lane, then thread c sums the lanes holding column c
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    red[wid][lane][q] = lane_ok ? pr[q] : A(0);
+    red[wid][lane][4 + q] = lane_ok ? px[q] : A(0);
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * M) {
+    const int c = threadIdx.x % M, which = threadIdx.x / M;
+    const int ctl = c / 4, q = c % 4;
+    double s = 0.0;
+    for (int w = 0; w < NW; ++w)
+      for (int l = ctl; l < RPW * G; l += G) s += (double)red[w][l][which * 4 + q];
+    part[threadIdx.x] = s;
+  }
+  const int cl = cluster_id();
+  cluster_sum(part, 2 * M, [&](int t, double v) {
+    const int which = t / M, c = t % M;
+    a.partN[(size_t)cl * 2 * MAXM + which * MAXM + c] = v;
+  });
+}
+
+// =======================================================================================
+// initial block and output
+// =======================================================================================
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  // SplitMix64 (Steele, Lea, Flood 2014): golden-ratio increment, then the finaliser
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+template <typename T>
+__global__ void k_init_block(int64_t n, int M, uint64_t seed, const double* x0, int x0_cols, T* Wr) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * M) return;
+  int64_t i = t / M;
+  int c = (int)(t % M);
+  double v;
+  if (x0 && c < x0_cols) {
+    v = x0[(int64_t)c * n + i];
+  } else {
+    // Box-Muller on two uniforms from the counter (i, c)
+    uint64_t h1 = splitmix64(seed ^ splitmix64((uint64_t)t * 2));
+    uint64_t h2 = splitmix64(seed ^ splitmix64((uint64_t)t * 2 + 1));
+    double u1 = ((h1 >> 11) + 1) * (1.0 / 9007199254740993.0);   // (0, 1]
+    double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);
+    v = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+  }
+  Wr[t] = (T)v;
+}
+
+template <typename T>
+__global__ void k_vmax(int64_t n, int M, int K, const T* X, unsigned long long* vmax) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * K) return;
+  int64_t i = t / K;
+  int c = (int)(t % K);
+  double v = fabs((double)X[i * M + c]);
+  atomicMax(vmax + c, (unsigned long long)__double_as_longlong(v));
+}
+
+template <typename T>
+__global__ void k_vidx(int64_t n, int M, int K, const T* X, const unsigned long long* vmax,
+                       unsigned long long* vidx) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * K) return;
+  int64_t i = t / K;
+  int c = (int)(t % K);
+  double v = fabs((double)X[i * M + c]);
+  if ((unsigned long long)__double_as_longlong(v) == vmax[c]) atomicMin(vidx + c, (unsigned long long)i);
+}
+
+template <typename T>
+__global__ void k_write_v(int64_t n, int M, int K, const T* X, const unsigned long long* vidx, double* V) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * K) return;
+  int c = (int)(t / n);
+  int64_t i = t % n;
+  unsigned long long r = vidx[c];
+  double s = (r < (unsigned long long)n && (double)X[(int64_t)r * M + c] < 0.0) ? -1.0 : 1.0;
+  V[t] = s * (double)X[i * M + c];
+}
+
+inline unsigned gridn(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// =======================================================================================
+// host driver
+// =======================================================================================
+template <typename T, int M>
+struct Solver {
+  Ctx* ctx;
+  cudaStream_t st;
+  const LobOp& op;
+  int K;
+  int64_t n;
+  DevBuf<T> X, AX, P, AP, W, AW, Wr;
+  DevBuf<unsigned char> small;
+  Small* sm = nullptr;
+  SmallT<T>* smt = nullptr;
+  State* state = nullptr;
+  int grid_rows = 0, grid_upd = 0, grid_gram = 0;
+  double tol;
+  int maxiter;
+  bool inverse_rr = true;
+  double tau = 1e-12, tau_p = 1e-16, tau_w = 1e-10;
+  int64_t nnz_a = 0;
+
+  Solver(Ctx* c, cudaStream_t s, const LobOp& o, int k) : ctx(c), st(s), op(o), K(k), n(o.n) {}
+
+  static int clusters_for(int64_t units, int per_cta, int max_ctas) {
+    int64_t ctas = (units + per_cta - 1) / per_cta;
+    int64_t cls = (ctas + CL - 1) / CL;
+    cls = std::max<int64_t>(1, std::min<int64_t>(cls, std::min(max_ctas / CL, MAXCL)));
+    return (int)cls;
+  }
+
+  mge_status setup() {
+    size_t blk = (size_t)n * M;
+    MGE_TRY(X.alloc(ctx, blk)); MGE_TRY(AX.alloc(ctx, blk));
+    MGE_TRY(P.alloc(ctx, blk)); MGE_TRY(AP.alloc(ctx, blk));
+    MGE_TRY(W.alloc(ctx, blk)); MGE_TRY(AW.alloc(ctx, blk));
+    MGE_TRY(Wr.alloc(ctx, blk));
+    size_t off_t = ((sizeof(Small) + 255) / 256) * 256;
+    size_t off_s = off_t + ((sizeof(SmallT<T>) + 255) / 256) * 256;
+    size_t bytes = off_s + sizeof(State);
+    MGE_TRY(small.alloc(ctx, bytes));
+    MGE_CUDA(ctx, cudaMemsetAsync(small.p, 0, bytes, st));
+    sm = reinterpret_cast<Small*>(small.p);
+    smt = reinterpret_cast<SmallT<T>*>(small.p + off_t);
+    state = reinterpret_cast<State*>(small.p + off_s);
+    const int spmm_rows_per_cta = SpmmShape<M>::RPW * (kThreads / 32);
+    int64_t sctas = (n + spmm_rows_per_cta - 1) / spmm_rows_per_cta;
+    grid_rows = (int)std::max<int64_t>(1, std::min<int64_t>(sctas, (int64_t)ctx->num_sms * 8));
+    constexpr int RPW = 32 / (M / 4);
+    const int rows_per_cta = RPW * (kThreads / 32);
+    const int max_red = std::min(2 * ctx->num_sms, MAXCL * CL);
+    grid_upd = CL * clusters_for(n, rows_per_cta, max_red);
+    grid_gram = CL * clusters_for(n, kTileRows * 4, max_red);
+    if (sizeof(T) == 4) { tau = 1e-6; tau_p = 1e-8; tau_w = 1e-4; }
+    // the inverse-pencil Rayleigh-Ritz needs G_A positive definite: A = L - mu Q + eps I with
+    // eps > 0, or Q with the constant vector deflated
+    inverse_rr = (sizeof(T) == 4) && (op.shift > 0.0 || op.deflate);
+    return MGE_OK;
+  }
+
+  size_t gram_smem(int nl, int n1, int n2, bool sym2, bool csum) {
+    size_t w = (size_t)nl * M + (size_t)n1 * M + (sym2 ? 0 : (size_t)n2 * M);
+    size_t s = kTileRows * w * sizeof(T) + kTileRows * sizeof(T);
+    int bl = nl * M / 4;
+    int nblk = bl * (n1 * M / 4) + (sym2 ? bl * (bl + 1) / 2 : bl * (n2 * M / 4));
+    int rs = std::max(1, kThreads / nblk);
+    size_t len = (size_t)nblk * 16;
+    size_t r = ((rs * len * sizeof(T) + 15) / 16) * 16 + (len + (csum ? (size_t)n2 * M : 0)) * sizeof(double);
+    return std::max(s, r);
+  }
+
+  void launch_gram(int nl, const T* const* L, int n1, const T* const* R1, int n2, const T* const* R2,
+                   bool sym2, bool weighted, double* out1, double* out2, int ld2, int stride2, bool csum) {
+    GramArgs<T> g{};
+    g.n = n; g.nl = nl; g.n1 = n1; g.n2 = n2;
+    for (int i = 0; i < 3; ++i) {
+      g.L[i] = i < nl ? L[i] : nullptr;
+      g.R1[i] = i < n1 ? R1[i] : nullptr;
+      g.R2[i] = i < n2 ? R2[i] : nullptr;
+    }
+    g.sym2 = sym2;
+    g.b = weighted ? static_cast<const T*>(op.b) : nullptr;
+    g.out1 = out1; g.out2 = out2; g.ld2 = ld2; g.stride2 = stride2;
+    g.csum = csum ? &sm->partC[0][0] : nullptr;
+    g.st = state;
+    size_t smem = gram_smem(nl, n1, n2, sym2, csum);
+    k_gram<T, M><<<grid_gram, kThreads, smem, st>>>(g);
+    MGE_LAUNCHED(ctx, 1);
+  }
+
+  // algorithmic bytes of one SpMM launch: A's column indices and values, the row pointers,
+  // the gathered block once, the projection blocks read, W and AW written
+  uint64_t spmm_bytes(bool hx, bool hp) const {
+    uint64_t blk = (uint64_t)n * M * sizeof(T);
+    uint64_t b = (uint64_t)nnz_a * (4 + sizeof(T)) + (uint64_t)(n + 1) * 8 + blk + 2 * blk;
+    if (hx) b += 2 * blk;
+    if (hp) b += 2 * blk;
+    return b;
+  }
+
+  mge_status launch_spmm(bool hx, bool hp, bool timed) {
+    SpmmArgs<T> s{};
+    s.n = n; s.ptr = op.ptr; s.col = op.col; s.val = static_cast<const T*>(op.val);
+    s.shift = (T)op.shift;
+    s.Wr = Wr.p;
+    s.X = hx ? X.p : nullptr; s.AX = hx ? AX.p : nullptr;
+    s.P = hp ? P.p : nullptr; s.AP = hp ? AP.p : nullptr;
+    s.sm = smt;
+    s.W = W.p; s.AW = AW.p;
+    s.st = state;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timed) {
+      if (ctx->ev_used >= ctx->ev_pool.size()) {
+        cudaEvent_t x, y;
+        MGE_CUDA(ctx, cudaEventCreate(&x));
+        MGE_CUDA(ctx, cudaEventCreate(&y));
+        ctx->ev_pool.push_back({x, y});
+      }
+      e0 = ctx->ev_pool[ctx->ev_used].first;
+      e1 = ctx->ev_pool[ctx->ev_used].second;
+      ctx->ev_used++;
+      ctx->ev_bytes.push_back(spmm_bytes(hx, hp));
+      MGE_CUDA(ctx, cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal));
+    }
+    k_spmm_w<T, M><<<grid_rows, kThreads, 0, st>>>(s);
+    MGE_LAUNCHED(ctx, 1);
+    if (timed) MGE_CUDA(ctx, cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal));
+    return MGE_OK;
+  }
+
+  void launch_rr_(int nb, int nx) {
+    RRArgs r{};
+    r.sm = sm; r.smt = smt; r.is_double = sizeof(T) == 8; r.ncl = grid_gram / CL;
+    r.M = M; r.nb = nb; r.nx = nx; r.tau = tau; r.tau_p = tau_p; r.st = state;
+    launch_rr(st, r, inverse_rr);
+    MGE_LAUNCHED(ctx, 1);
+  }
+
+  void launch_update(int nb, bool init, bool produce_p) {
+    UpdArgs<T> u{};
+    u.n = n; u.nb = nb;
+    if (init) { u.S[0] = W.p; u.AS[0] = AW.p; }
+    else {
+      u.S[0] = X.p; u.AS[0] = AX.p;
+      u.S[1] = W.p; u.AS[1] = AW.p;
+      u.S[2] = P.p; u.AS[2] = AP.p;
+    }
+    u.Xo = X.p; u.AXo = AX.p; u.Po = P.p; u.APo = AP.p;
+    u.produce_p = produce_p;
+    u.smt = smt;
+    u.b = static_cast<const T*>(op.b);
+    u.dinv = static_cast<const T*>(op.dinv);
+    u.Wr = Wr.p;
+    u.partN = &sm->partN[0][0];
+    u.st = state;
+    k_update<T, M><<<grid_upd, kThreads, 0, st>>>(u);
+    MGE_LAUNCHED(ctx, 1);
+  }
+
+  void launch_wprep_(bool hx, bool hp, bool check) {
+    WprepArgs w{};
+    w.sm = sm; w.smt = smt; w.is_double = sizeof(T) == 8;
+    w.ncl_w = grid_gram / CL; w.ncl_n = grid_upd / CL;
+    w.M = M; w.K = K; w.has_x = hx; w.has_p = hp; w.check = check;
+    w.deflate = op.deflate; w.n = n; w.tol = tol; w.norm = op.norm; w.bmax = op.bmax;
+    w.tau_w = tau_w; w.maxiter = maxiter; w.st = state;
+    launch_wprep(st, w, sizeof(T) == 8);
+    MGE_LAUNCHED(ctx, 1);
+  }
+
+  void launch_gram_w(bool hx, bool hp) {
+    const T* L[3];
+    int nl = 0;
+    if (hx) L[nl++] = X.p;
+    if (hp) L[nl++] = P.p;
+    L[nl++] = Wr.p;
+    const T* R2[1] = {Wr.p};
+    launch_gram(nl, L, 0, nullptr, 1, R2, false, op.b != nullptr, nullptr, &sm->partW[0][0], MAXM,
+                MAXS * MAXM, op.deflate);
+  }
+
+  void launch_gram_s(int nb) {
+    const T* L[3] = {X.p, W.p, P.p};
+    const T* R[3] = {AX.p, AW.p, AP.p};
+    if (nb == 1) { L[0] = W.p; R[0] = AW.p; }
+    launch_gram(nb, L, nb, R, nb, L, true, op.b != nullptr, &sm->partA[0][0], &sm->partB[0][0], MAXS,
+                MAXS * MAXS, false);
+  }
+
+  mge_status iteration(int nb, bool timed) {
+    bool hp = nb == 3;
+    MGE_TRY(launch_spmm(true, hp, timed));
+    launch_gram_s(nb);
+    launch_rr_(nb, M);
+    launch_update(nb, false, true);
+    launch_gram_w(true, true);
+    launch_wprep_(true, true, true);
+    return MGE_OK;
+  }
+
+  mge_status run(int check_every, bool use_graph, uint64_t seed, const double* x0, int x0_cols,
+                 double* V_out, LobResult* res) {
+    cudaEvent_t e0, e1;
+    MGE_CUDA(ctx, cudaEventCreate(&e0));
+    MGE_CUDA(ctx, cudaEventCreate(&e1));
+    MGE_CUDA(ctx, cudaEventRecord(e0, st));
+    const bool timed = ctx->timing;
+    // --- init: W_raw = X0, normalise, Rayleigh-Ritz on span(W) ---
+    k_init_block<T><<<gridn(n * M, 256), 256, 0, st>>>(n, M, seed, x0, x0_cols, Wr.p);
+    MGE_LAUNCHED(ctx, 1);
+    launch_gram_w(false, false);
+    launch_wprep_(false, false, false);
+    MGE_TRY(launch_spmm(false, false, timed));
+    launch_gram_s(1);
+    launch_rr_(1, 0);
+    launch_update(1, true, false);
+    launch_gram_w(true, false);
+    launch_wprep_(true, false, true);
+    // --- first iteration: S = [X W] ---
+    MGE_TRY(launch_spmm(true, false, timed));
+    launch_gram_s(2);
+    launch_rr_(2, M);
+    launch_update(2, false, true);
+    launch_gram_w(true, true);
+    launch_wprep_(true, true, true);
+    MGE_CUDA(ctx, cudaGetLastError());
+    State* hst = nullptr;
+    MGE_CUDA(ctx, cudaMallocHost(&hst, sizeof(State)));
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    mge_status status = MGE_OK;
+    if (check_every < 1) check_every = 1;
+    auto finish_timing = [&]() -> mge_status {
+      if (!timed) return MGE_OK;
+      MGE_CUDA(ctx, cudaStreamSynchronize(st));
+      for (size_t i = 0; i < ctx->ev_used; ++i) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, ctx->ev_pool[i].first, ctx->ev_pool[i].second) == cudaSuccess) {
+          ctx->spmm_ms += ms;
+          ctx->spmm_launches += 1;
+          ctx->spmm_bytes += ctx->ev_bytes[i];
+        }
+      }
+      ctx->ev_used = 0;
+      ctx->ev_bytes.clear();
+      return MGE_OK;
+    };
+    MGE_TRY(finish_timing());
+    bool graph_ok = use_graph;
+    if (graph_ok) {
+      cudaStreamCaptureStatus cs;
+      MGE_CUDA(ctx, cudaStreamIsCapturing(st, &cs));
+      if (cs != cudaStreamCaptureStatusNone) graph_ok = false;
+    }
+    if (graph_ok) {
+      MGE_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      uint64_t before = ctx->kernel_launches;
+      mge_status cap = MGE_OK;
+      for (int i = 0; i < check_every && cap == MGE_OK; ++i) cap = iteration(3, timed && i == 0);
+      cudaError_t ce = cudaStreamEndCapture(st, &graph);
+      if (cap != MGE_OK) return cap;
+      if (ce != cudaSuccess) { set_error(ctx, "graph capture failed: %s", cudaGetErrorString(ce)); return MGE_EDEVICE; }
+      ctx->kernel_launches = before;
+      MGE_CUDA(ctx, cudaGraphInstantiate(&gexec, graph, 0));
+      if (timed) { ctx->ev_used = 0; ctx->ev_bytes.clear(); }
+    }
+    const uint64_t per_chunk = (uint64_t)check_every * 6;
+    for (;;) {
+      MGE_CUDA(ctx, cudaMemcpyAsync(hst, state, sizeof(State), cudaMemcpyDeviceToHost, st));
+      MGE_CUDA(ctx, cudaStreamSynchronize(st));
+      if (hst->done != DONE_RUNNING) break;
+      if (graph_ok) {
+        if (timed) {
+          ctx->ev_used = 1;
+          ctx->ev_bytes.assign(1, spmm_bytes(true, true));
+        }
+        MGE_CUDA(ctx, cudaGraphLaunch(gexec, st));
+        ctx->kernel_launches += per_chunk;
+        MGE_TRY(finish_timing());
+      } else {
+        for (int i = 0; i < check_every; ++i) MGE_TRY(iteration(3, timed));
+        MGE_CUDA(ctx, cudaGetLastError());
+        MGE_TRY(finish_timing());
+      }
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    MGE_CUDA(ctx, cudaEventRecord(e1, st));
+    if (hst->done == DONE_ERROR) {
+      status = (mge_status)hst->err;
+      set_error(ctx, "LOBPCG stopped at iteration %d: %s (stage %d, kept %d)", hst->iter,
+                mge_strerror(status), hst->bad_stage, hst->kept);
+    } else if (hst->done == DONE_MAXITER) {
+      status = MGE_ENOTCONVERGED;
+    }
+    if (getenv("MGE_PHASES")) {
+      fprintf(stderr, "[mge] n=%lld M=%d iters=%d rr_clk:", (long long)n, M, hst->iter);
+      for (int i = 0; i < 12; ++i) fprintf(stderr, " %lld", hst->rr_clk[i]);
+      fprintf(stderr, " | wprep_clk:");
+      for (int i = 0; i < 4; ++i) fprintf(stderr, " %lld", hst->wp_clk[i]);
+      fprintf(stderr, "\n");
+    }
+    res->iters = hst->iter;
+    res->drops = hst->drops;
+    res->lambda.assign(hst->lambda, hst->lambda + K);
+    res->eta.assign(hst->eta, hst->eta + K);
+    if (V_out && (status == MGE_OK || status == MGE_ENOTCONVERGED)) {
+      MGE_CUDA(ctx, cudaMemsetAsync(sm->vmax, 0, sizeof(sm->vmax), st));
+      MGE_CUDA(ctx, cudaMemsetAsync(sm->vidx, 0xff, sizeof(sm->vidx), st));
+      k_vmax<T><<<gridn(n * K, 256), 256, 0, st>>>(n, M, K, X.p, sm->vmax);
+      k_vidx<T><<<gridn(n * K, 256), 256, 0, st>>>(n, M, K, X.p, sm->vmax, sm->vidx);
+      k_write_v<T><<<gridn(n * K, 256), 256, 0, st>>>(n, M, K, X.p, sm->vidx, V_out);
+      MGE_LAUNCHED(ctx, 3);
+      MGE_CUDA(ctx, cudaGetLastError());
+    }
+    MGE_CUDA(ctx, cudaStreamSynchronize(st));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    res->ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeHost(hst);
+    res->status = status;
+    return status;
+  }
+};
+
+template <typename T, int M>
+mge_status solve_m(Ctx* ctx, cudaStream_t st, const LobOp& op, int K, double tol, int maxiter, uint64_t seed,
+                   int check_every, bool use_graph, const double* x0, int x0_cols, double* V_out,
+                   LobResult* res) {
+  Solver<T, M> s(ctx, st, op, K);
+  s.tol = tol;
+  s.maxiter = maxiter;
+  MGE_TRY(s.setup());
+  int64_t nnz = 0;
+  MGE_CUDA(ctx, cudaMemcpyAsync(&nnz, op.ptr + op.n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  s.nnz_a = nnz;
+  MGE_CUDA(ctx, cudaFuncSetAttribute(k_gram<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+  MGE_CUDA(ctx, rr_configure());
+  return s.run(check_every, use_graph, seed, x0, x0_cols, V_out, res);
+}
+
+template <typename T>
+mge_status solve_t(Ctx* ctx, cudaStream_t st, const LobOp& op, int K, int m, double tol, int maxiter,
+                   uint64_t seed, int check_every, bool use_graph, const double* x0, int x0_cols,
+                   double* V_out, LobResult* res) {
+  switch (m) {
+    case 4: return solve_m<T, 4>(ctx, st, op, K, tol, maxiter, seed, check_every, use_graph, x0, x0_cols, V_out, res);
+    case 8: return solve_m<T, 8>(ctx, st, op, K, tol, maxiter, seed, check_every, use_graph, x0, x0_cols, V_out, res);
+    case 12: return solve_m<T, 12>(ctx, st, op, K, tol, maxiter, seed, check_every, use_graph, x0, x0_cols, V_out, res);
+    case 16: return solve_m<T, 16>(ctx, st, op, K, tol, maxiter, seed, check_every, use_graph, x0, x0_cols, V_out, res);
+    case 24: return solve_m<T, 24>(ctx, st, op, K, tol, maxiter, seed, check_every, use_graph, x0, x0_cols, V_out, res);
+    default:
+      set_error(ctx, "unsupported block width %d", m);
+      return MGE_EINVAL;
+  }
+}
+
+template <typename T, int M>
+mge_status apply_m(Ctx* ctx, cudaStream_t st, const LobOp& op, const void* X, void* Y) {
+  SpmmArgs<T> s{};
+  s.n = op.n; s.ptr = op.ptr; s.col = op.col; s.val = static_cast<const T*>(op.val);
+  s.shift = (T)op.shift; s.Wr = static_cast<const T*>(X); s.AW = static_cast<T*>(Y);
+  s.W = nullptr; s.sm = nullptr; s.st = nullptr;
+  const int rows_per_cta = SpmmShape<M>::RPW * (kThreads / 32);
+  int64_t ctas = (op.n + rows_per_cta - 1) / rows_per_cta;
+  int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, (int64_t)ctx->num_sms * 8));
+  k_spmm_w<T, M><<<grid, kThreads, 0, st>>>(s);
+  MGE_LAUNCHED(ctx, 1);
+  MGE_CUDA(ctx, cudaGetLastError());
+  return MGE_OK;
+}
+
+}  // namespace
+}  // namespace lob
+
+mge_status lobpcg_solve(Ctx* ctx, cudaStream_t st, const LobOp& op, int precision, int K, int m, double tol,
+                        int maxiter, uint64_t seed, int check_every, bool use_graph, const double* x0_dev,
+                        int x0_cols, double* V_out, LobResult* res) {
+  using namespace lob;
+  if (m > MAXM || m < 4) { set_error(ctx, "block width %d out of range", m); return MGE_EINVAL; }
+  if (K < 1 || K > m) { set_error(ctx, "K = %d out of range for block width %d", K, m); return MGE_EINVAL; }
+  if (op.n < 2 * m) { set_error(ctx, "n = %lld too small for block width %d", (long long)op.n, m); return MGE_EINVAL; }
+  if (precision == MGE_FP64)
+    return solve_t<double>(ctx, st, op, K, m, tol, maxiter, seed, check_every, use_graph, x0_dev, x0_cols, V_out, res);
+  if (precision == MGE_FP32)
+    return solve_t<float>(ctx, st, op, K, m, tol, maxiter, seed, check_every, use_graph, x0_dev, x0_cols, V_out, res);
+  set_error(ctx, "precision %d not supported by the solver", precision);
+  return MGE_EINVAL;
+}
+
+mge_status spmm_apply(Ctx* ctx, cudaStream_t st, const LobOp& op, int precision, int m, const void* X, void* Y) {
+  using namespace lob;
+  if (precision == MGE_FP64) {
+    switch (m) {
+      case 4: return apply_m<double, 4>(ctx, st, op, X, Y);
+      case 8: return apply_m<double, 8>(ctx, st, op, X, Y);
+      case 12: return apply_m<double, 12>(ctx, st, op, X, Y);
+      case 16: return apply_m<double, 16>(ctx, st, op, X, Y);
+      case 24: return apply_m<double, 24>(ctx, st, op, X, Y);
+    }
+  } else if (precision == MGE_FP32) {
+    switch (m) {
+      case 4: return apply_m<float, 4>(ctx, st, op, X, Y);
+      case 8: return apply_m<float, 8>(ctx, st, op, X, Y);
+      case 12: return apply_m<float, 12>(ctx, st, op, X, Y);
+      case 16: return apply_m<float, 16>(ctx, st, op, X, Y);
+      case 24: return apply_m<float, 24>(ctx, st, op, X, Y);
+    }
+  }
+  set_error(ctx, "unsupported precision %d / width %d for apply", precision, m);
+  return MGE_EINVAL;
+}
+
+}  // namespace mge

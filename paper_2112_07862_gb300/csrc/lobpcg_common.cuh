@@ -1,0 +1,172 @@
+// Device-side state, scratch layout and helpers shared by the LOBPCG kernels (lobpcg.cu)
+// and the small dense kernels (rr.cu).
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "mge_internal.cuh"
+
+namespace mge {
+namespace lob {
+
+namespace cg = cooperative_groups;
+
+constexpr int MAXM = 24;             // widest block
+constexpr int MAXS = 3 * MAXM;       // widest Rayleigh-Ritz basis [X W P]
+constexpr int CL = 8;                // CTAs per cluster in the reducing kernels
+constexpr int MAXCL = 64;            // clusters per reducing launch (grid <= 512 CTAs)
+constexpr int kThreads = 256;
+
+enum : int { DONE_RUNNING = 0, DONE_CONVERGED = 1, DONE_ERROR = 2, DONE_MAXITER = 3 };
+
+struct State {
+  int done;
+  int iter;
+  int err;
+  int drops;
+  int kept;
+  int bad_stage;     // 1: Rayleigh-Ritz input, 2: residual / Ritz values, 3: W Gram, 4: RR output
+  int pad[2];
+  long long rr_clk[16];     // clock64 deltas at the phase boundaries of the last Rayleigh-Ritz
+  long long wp_clk[8];      // and of the last wprep (diagnostics)
+  double lambda[MAXM];
+  double eta[MAXM];
+};
+
+// FP64 results of the small kernels and the per-cluster partial sums they consume.
+struct Small {
+  double partA[MAXCL][MAXS * MAXS];   // G_A = S^T A S, per cluster
+  double partB[MAXCL][MAXS * MAXS];   // G_B = S^T B S (block-upper part), per cluster
+  double partW[MAXCL][MAXS * MAXM];   // [X' P' W_raw]^T B W_raw, per cluster
+  double partC[MAXCL][MAXM];          // column sums of W_raw (deflation), per cluster
+  double partN[MAXCL][2 * MAXM];      // ||r_k||^2 and ||x_k||^2, per cluster
+  double Cx[MAXS * MAXM], Cp[MAXS * MAXM];
+  double lam[MAXM];
+  double Linv[MAXM * MAXM], Mx[MAXM * MAXM], Mp[MAXM * MAXM], cmean[MAXM];
+  unsigned long long vmax[MAXM];
+  unsigned long long vidx[MAXM];
+};
+
+// Block-precision copies the streaming kernels read.
+template <typename T>
+struct SmallT {
+  T Cx[MAXS * MAXM], Cp[MAXS * MAXM];
+  T lam[MAXM];
+  T Linv[MAXM * MAXM], Mx[MAXM * MAXM], Mp[MAXM * MAXM], cmean[MAXM];
+};
+
+// ---- 4-wide vector access -------------------------------------------------------------
+__device__ __forceinline__ void ld4(const float* p, float v[4]) {
+  float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double v[4]) {
+  double2 a = reinterpret_cast<const double2*>(p)[0];
+  double2 b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float v[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double v[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void ldg4(const float* p, float v[4]) {
+  float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ldg4(const double* p, double v[4]) {
+  double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+// Sums `len` doubles that every CTA of the cluster holds at `buf` (shared memory) and stores
+// the cluster total through store(index, value).  Rank r reduces the slice r of the vector,
+// reading all peers' copies through distributed shared memory.
+template <typename F>
+__device__ __forceinline__ void cluster_sum(const double* buf, int len, F store) {
+  cg::cluster_group cl = cg::this_cluster();
+  cl.sync();
+  const int r = (int)cl.block_rank();
+  const int nr = (int)cl.num_blocks();
+  const int per = (len + nr - 1) / nr;
+  const int lo = r * per, hi = min(len, lo + per);
+  for (int t = lo + (int)threadIdx.x; t < hi; t += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nr; ++q) s += cl.map_shared_rank(buf, q)[t];
+    store(t, s);
+  }
+  cl.sync();   // peers keep their shared memory until every slice is read
+}
+
+__device__ __forceinline__ int cluster_id() { return blockIdx.x / CL; }
+
+// Sum of p[c * stride] for c < n with eight loads in flight (the partial sums sit in L2; a
+// plain dependent loop pays the full load latency per term).
+__device__ __forceinline__ double sum_strided(const double* p, int n, size_t stride) {
+  double s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0, s6 = 0, s7 = 0;
+  int c = 0;
+  for (; c + 8 <= n; c += 8) {
+    double v0 = p[(size_t)(c + 0) * stride], v1 = p[(size_t)(c + 1) * stride];
+    double v2 = p[(size_t)(c + 2) * stride], v3 = p[(size_t)(c + 3) * stride];
+    double v4 = p[(size_t)(c + 4) * stride], v5 = p[(size_t)(c + 5) * stride];
+    double v6 = p[(size_t)(c + 6) * stride], v7 = p[(size_t)(c + 7) * stride];
+    s0 += v0; s1 += v1; s2 += v2; s3 += v3; s4 += v4; s5 += v5; s6 += v6; s7 += v7;
+  }
+  for (; c < n; ++c) s0 += p[(size_t)c * stride];
+  return ((s0 + s1) + (s2 + s3)) + ((s4 + s5) + (s6 + s7));
+}
+
+// FP64 reciprocal square root from an FP32 seed and two Newton steps
+// (y <- y (3 - x y^2) / 2); avoids the long-latency FP64 division/sqrt sequences.
+__device__ __forceinline__ double drsqrt(double x) {
+  double y = (double)rsqrtf((float)x);
+  y = y * (1.5 - 0.5 * x * y * y);
+  y = y * (1.5 - 0.5 * x * y * y);
+  return y;
+}
+// FP64 reciprocal from an FP32 seed and two Newton steps (y <- y (2 - x y)).
+__device__ __forceinline__ double drcp(double x) {
+  double y = (double)(1.0f / (float)x);
+  y = y * (2.0 - x * y);
+  y = y * (2.0 - x * y);
+  return y;
+}
+
+
+// Arguments of the single-CTA kernels in rr.cu (launched from lobpcg.cu).
+struct RRArgs {
+  Small* sm;
+  void* smt;            // SmallT<float> or SmallT<double>
+  int is_double;
+  int ncl;              // clusters that wrote Gram partials
+  int M, nb, nx;        // basis: nb blocks of M columns, the first nx of which are X
+  double tau;           // dependence threshold (pivot^2 of a unit-diagonal Gram)
+  double tau_p;         // threshold for dropping an empty P direction
+  State* st;
+};
+
+struct WprepArgs {
+  Small* sm;
+  void* smt;
+  int is_double;
+  int ncl_w;            // clusters that wrote W-side Gram partials
+  int ncl_n;            // clusters that wrote norm partials
+  int M, K;
+  int has_x, has_p;
+  int check;
+  int deflate;
+  int64_t n;
+  double tol, norm, bmax, tau_w;
+  int maxiter;
+  State* st;
+};
+
+cudaError_t rr_configure();
+void launch_rr(cudaStream_t st, const RRArgs& a, bool inverse_form);
+void launch_wprep(cudaStream_t st, const WprepArgs& a, bool fp64);
+
+}  // namespace lob
+}  // namespace mge

@@ -1,0 +1,160 @@
+// Internal declarations shared by the libmge translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mge.h"
+
+namespace mge {
+
+// ---------------------------------------------------------------------------------------
+// error plumbing: every CUDA call is checked and turned into an mge_status
+// ---------------------------------------------------------------------------------------
+struct Ctx;
+void set_error(Ctx* ctx, const char* fmt, ...);
+
+#define MGE_CUDA(ctx, call)                                                              \
+  do {                                                                                   \
+    cudaError_t _e = (call);                                                             \
+    if (_e != cudaSuccess) {                                                             \
+      ::mge::set_error((ctx), "%s:%d %s: %s", __FILE__, __LINE__, #call,                 \
+                       cudaGetErrorString(_e));                                          \
+      return (_e == cudaErrorMemoryAllocation) ? MGE_ENOMEM : MGE_EDEVICE;               \
+    }                                                                                    \
+  } while (0)
+
+#define MGE_TRY(expr)                                                                    \
+  do {                                                                                   \
+    mge_status _s = (expr);                                                              \
+    if (_s != MGE_OK) return _s;                                                         \
+  } while (0)
+
+// Launch bookkeeping: every kernel launch goes through this so the context can count it.
+#define MGE_LAUNCHED(ctx, k) ((ctx)->kernel_launches += (k))
+
+// ---------------------------------------------------------------------------------------
+// device memory: plain cudaMallocAsync-free allocations accounted against a budget
+// ---------------------------------------------------------------------------------------
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t budget = 0;               // 0 = unlimited
+  std::atomic<size_t> in_use{0};
+  std::atomic<uint64_t> kernel_launches{0};
+  // SpMM timing (roofline measurement)
+  bool timing = false;
+  uint64_t spmm_launches = 0;
+  double spmm_ms = 0.0;
+  uint64_t spmm_bytes = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  size_t ev_used = 0;
+  std::vector<uint64_t> ev_bytes;
+  std::string last_error;
+  std::mutex err_mu;
+  int num_sms = 0;
+  void* serve = nullptr;           // serving state (serve.cu)
+  void* self = nullptr;            // the owning mge_ctx*
+};
+
+mge_status dev_alloc(Ctx* ctx, void** p, size_t bytes);
+void dev_free(Ctx* ctx, void* p, size_t bytes);
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  Ctx* ctx = nullptr;
+  mge_status alloc(Ctx* c, size_t count) {
+    release();
+    ctx = c;
+    n = count;
+    if (count == 0) return MGE_OK;
+    void* q = nullptr;
+    mge_status s = dev_alloc(c, &q, count * sizeof(T));
+    if (s != MGE_OK) { n = 0; return s; }
+    p = static_cast<T*>(q);
+    return MGE_OK;
+  }
+  void release() {
+    if (p) dev_free(ctx, p, n * sizeof(T));
+    p = nullptr;
+    n = 0;
+  }
+  ~DevBuf() { release(); }
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+};
+
+// ---------------------------------------------------------------------------------------
+// operators built by mge_build_graph_ops (everything device resident)
+// ---------------------------------------------------------------------------------------
+struct Ops {
+  Ctx* ctx = nullptr;
+  int64_t n = 0, nnz_w = 0, nnz_a = 0, nnz_q = 0;
+  DevBuf<int64_t> w_ptr;  DevBuf<int32_t> w_col;  DevBuf<double> w_val;
+  DevBuf<int32_t> T;
+  DevBuf<int64_t> q_ptr;  DevBuf<int32_t> q_col;  DevBuf<double> q_val;
+  DevBuf<int64_t> a_ptr;  DevBuf<int32_t> a_col;  DevBuf<double> a_val;
+  DevBuf<float>   q_val32, a_val32;          // FP32 copies for the reduced-precision forms
+  DevBuf<double>  b, dinv_a, dinv_q;         // B diagonal, Jacobi preconditioners
+  DevBuf<float>   b32, dinv_a32, dinv_q32;
+  double eps = 0, mu = 0, norm_a = 0, norm_q = 0, bmax = 1;
+  int degenerate = 0, ncomp = 1, eps_iters = 0;
+  double eps_resid = 0, build_ms = 0;
+};
+
+// ---------------------------------------------------------------------------------------
+// LOBPCG operator description handed to the solver
+// ---------------------------------------------------------------------------------------
+struct LobOp {
+  int64_t n = 0;
+  const int64_t* ptr = nullptr;
+  const int32_t* col = nullptr;
+  const void* val = nullptr;       // double* or float* by precision
+  double shift = 0;                // A = (Laplacian part) + shift * I  (eps for A, 0 for Q)
+  const void* b = nullptr;         // NULL = identity B
+  const void* dinv = nullptr;      // Jacobi preconditioner diag(A)^-1
+  double norm = 1, bmax = 1;       // ||A||_G and max b for the backward error
+  bool deflate = false;            // keep blocks orthogonal to the constant vector
+};
+
+struct LobResult {
+  mge_status status = MGE_OK;
+  int iters = 0;
+  int drops = 0;
+  std::vector<double> lambda;      // [K]
+  std::vector<double> eta;         // [K]
+  double ms = 0;
+};
+
+// Runs LOBPCG; V_out (device, FP64 column-major [n x K]) may be NULL.
+mge_status lobpcg_solve(Ctx* ctx, cudaStream_t st, const LobOp& op, int precision, int K, int m,
+                        double tol, int maxiter, uint64_t seed, int check_every, bool use_graph,
+                        const double* x0_dev /*col-major n x x0_cols*/, int x0_cols,
+                        double* V_out, LobResult* res);
+
+mge_status spmm_apply(Ctx* ctx, cudaStream_t st, const LobOp& op, int precision, int m,
+                      const void* X, void* Y);
+
+// supported block widths
+inline int round_block_width(int m) {
+  const int w[] = {4, 8, 12, 16, 24, 32};
+  for (int x : w) if (m <= x) return x;
+  return -1;
+}
+
+inline int ceil_div_i(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace mge
+
+struct mge_ctx { mge::Ctx impl; };
+struct mge_ops { mge::Ops impl; };

@@ -1,0 +1,943 @@
+// Small dense kernels of the LOBPCG iteration (Sec. 4.3): Rayleigh-Ritz on the basis
+// S = [X W P] and the preparation of the next W block.  One CTA each.
+//
+// Rayleigh-Ritz solves G_A c = theta G_B c (G_A = S^T A S, G_B = S^T B S) for the m smallest
+// theta.  Two forms:
+//
+//  * k_rr_inv (FP32 and BF16 blocks).  FP64 sums of the per-cluster Gram partials, FP64
+//    scaling to unit G_A diagonal, then the inverse pencil in FP32: with G^_A = L L^T,
+//    M = L^-1 G^_B L^-T has eigenvalues mu = 1/theta, so the wanted (smallest) theta are the
+//    largest mu, which a backward-stable FP32 eigensolver gets to relative accuracy ~u times
+//    the ratio mu_max / mu (the spread of the wanted eigenvalues only).  A plain FP32
+//    eigensolve of (G_A, G_B) would give the small theta only to absolute accuracy
+//    u ||G_A||.  Eigenpairs of M: Householder tridiagonalisation, multisection bisection for
+//    the m largest eigenvalues, inverse iteration and CGS2 for their vectors.
+//  * k_rr_jacobi (FP64 blocks, and operators with a zero shift, for which G_A may be
+//    singular).  FP64 Cholesky of G^_B with dropping, reduction to standard form, cyclic
+//    two-sided Jacobi.
+//
+// Both drop basis directions that are numerically dependent (pivots below a threshold) and
+// return C_x (Ritz vectors, G_B-orthonormal), Lambda, and C_p (the next P: the W/P part of
+// the Ritz coefficients made G_B-orthogonal to C_x and G_B-orthonormal).
+#include "lobpcg_common.cuh"
+
+#include <cmath>
+
+namespace mge {
+namespace lob {
+
+// ---------------------------------------------------------------------------------------
+// shared: sum the cluster partials into gA, gB (FP64, row-major, leading dimension ld)
+// ---------------------------------------------------------------------------------------
+__device__ bool load_grams(const RRArgs& a, double* gA, double* gB, int n, int ld) {
+  __shared__ int nonfinite;
+  if (threadIdx.x == 0) nonfinite = 0;
+  const Small* sm = a.sm;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int i = t / n, j = t % n;
+    int bi = i / 4, bj = j / 4;
+    int si = (bi <= bj) ? i : j, sj = (bi <= bj) ? j : i;
+    gA[i * ld + j] = sum_strided(&sm->partA[0][i * MAXS + j], a.ncl, MAXS * MAXS);
+    gB[i * ld + j] = sum_strided(&sm->partB[0][si * MAXS + sj], a.ncl, MAXS * MAXS);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int i = t / n, j = t % n;
+    if (i < j) {
+      double va = 0.5 * (gA[i * ld + j] + gA[j * ld + i]);
+      gA[i * ld + j] = va; gA[j * ld + i] = va;
+      if (i / 4 == j / 4) {
+        double vb = 0.5 * (gB[i * ld + j] + gB[j * ld + i]);
+        gB[i * ld + j] = vb; gB[j * ld + i] = vb;
+      }
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int i = t / n, j = t % n;
+    if (!isfinite(gA[i * ld + j]) || !isfinite(gB[i * ld + j])) nonfinite = 1;
+  }
+  __syncthreads();
+  return nonfinite == 0;
+}
+
+// In-place Cholesky (lower) of the leading n x n block, dropping column j when its pivot^2
+// <= tau[j] or keep[j] == 0 (dropped columns and rows are zeroed); rd[j] = 1 / L_jj.
+template <typename R>
+__device__ void chol_drop(R* S, int ld, int n, const R* tau, int* keep, R* rd) {
+  __shared__ R piv;
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      R v = S[j * ld + j];
+      if (keep[j] && v > tau[j] && isfinite((double)v)) {
+        piv = sqrt(v);
+        S[j * ld + j] = piv;
+        rd[j] = R(1) / piv;
+      } else {
+        keep[j] = 0;
+        piv = R(0);
+        S[j * ld + j] = R(0);
+        rd[j] = R(0);
+      }
+    }
+    __syncthreads();
+    const R p = piv;
+    const R rp = rd[j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) S[i * ld + j] = (p > R(0)) ? S[i * ld + j] * rp : R(0);
+    __syncthreads();
+    if (p > R(0)) {
+      const int m = n - j - 1;
+      for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+        int i = j + 1 + t / m, k = j + 1 + t % m;
+        if (k <= i) S[i * ld + k] -= S[i * ld + j] * S[k * ld + j];
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int i = t / n, k = t % n;
+    if (k > i) S[i * ld + k] = R(0);
+  }
+  __syncthreads();
+}
+
+template <typename T, typename R>
+__device__ void store_coeffs(const RRArgs& a) {
+  SmallT<T>* o = static_cast<SmallT<T>*>(a.smt);
+  const Small* sm = a.sm;
+  for (int t = threadIdx.x; t < MAXS * MAXM; t += blockDim.x) { o->Cx[t] = (T)sm->Cx[t]; o->Cp[t] = (T)sm->Cp[t]; }
+  for (int t = threadIdx.x; t < MAXM; t += blockDim.x) o->lam[t] = (T)sm->lam[t];
+}
+
+// ---------------------------------------------------------------------------------------
+// Sturm count: eigenvalues of the symmetric tridiagonal (d, e) below x
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int sturm_count(const float* d, const float* e2, int k, float x, float pivmin) {
+  int c = 0;
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  c += q < 0.f;
+  for (int i = 1; i < k; ++i) {
+    q = (d[i] - x) - __fdividef(e2[i - 1], q);
+    if (fabsf(q) < pivmin) q = -pivmin;
+    c += q < 0.f;
+  }
+  return c;
+}
+
+// ---------------------------------------------------------------------------------------
+// fast form: FP32 inverse pencil (see the file comment)
+// ---------------------------------------------------------------------------------------
+constexpr int kRRThreads = 512;
+
+__global__ void __launch_bounds__(kRRThreads) k_rr_inv(RRArgs a) {
+  if (a.st->done) return;
+  long long clk0 = clock64();
+#define RR_MARK(k) do { __syncthreads(); if (threadIdx.x == 0) a.st->rr_clk[k] = clock64() - clk0; } while (0)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M = a.M, n = a.nb * a.M, nx = a.nx;
+  const int ldd = n + 1;         // FP64 leading dimension
+  const int ldf = n + 1;         // FP32 leading dimension
+  double* gA = reinterpret_cast<double*>(smem_raw);
+  double* gB = gA + n * ldd;
+  float* Lf = reinterpret_cast<float*>(gB + n * ldd);   // Cholesky factor of G^_A (compacted)
+  float* Mf = Lf + n * ldf;                              // M = L^-1 G^_B L^-T (kept for C_p)
+  float* Hf = Mf + n * ldf;                              // tridiagonalisation workspace
+  float* Yf = Hf + n * ldf;                              // eigenvectors of M, k x MAXM
+  float* scr = Yf + n * MAXM;                            // inverse-iteration scratch, 6 x k per vector
+  __shared__ double dsc[MAXS];
+  __shared__ float tauv[MAXS], rd[MAXS], td[MAXS], te[MAXS], te2[MAXS], ht[MAXS], wv[MAXS], pv[MAXS];
+  __shared__ float mu[MAXM], dots[MAXM], gp[MAXM * MAXM], rdp[MAXM], taup[MAXM];
+  __shared__ int keep[MAXS], idx[MAXS], pkeep[MAXM];
+  __shared__ int kcount, bad;
+  __shared__ float sh_f[4];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+
+  RR_MARK(1);
+  if (!load_grams(a, gA, gB, n, ldd)) {
+    if (threadIdx.x == 0) { a.st->done = DONE_ERROR; a.st->err = MGE_ENOTFINITE; a.st->bad_stage = 1; }
+    return;
+  }
+  // 1. scale to unit G_A diagonal; columns with empty A or B norm are dead
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double ga = gA[i * ldd + i], gb = gB[i * ldd + i];
+    bool live = ga > 1e-30 && gb > 1e-30 && ga < 1e30 && gb < 1e30;
+    dsc[i] = live ? drsqrt(ga) : 0.0;
+    keep[i] = live ? 1 : 0;
+    tauv[i] = (float)a.tau;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int i = t / n, j = t % n;
+    double s = dsc[i] * dsc[j];
+    Hf[i * ldf + j] = (float)(gA[i * ldd + j] * s);   // G^_A
+    Mf[i * ldf + j] = (float)(gB[i * ldd + j] * s);   // G^_B
+  }
+  __syncthreads();
+  RR_MARK(2);
+  // 2. Cholesky of G^_A with dropping
+  chol_drop<float>(Hf, ldf, n, tauv, keep, rd);
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int i = 0; i < n; ++i) if (keep[i]) idx[c++] = i;
+    kcount = c;
+  }
+  __syncthreads();
+  const int k = kcount;
+  if (k < M) {
+    if (threadIdx.x == 0) { a.st->done = DONE_ERROR; a.st->err = MGE_ECHOLESKY; a.st->kept = k; }
+    return;
+  }
+  if (threadIdx.x == 0 && k < n) atomicAdd(&a.st->drops, 1);
+  // compact: L -> Lf, G^_B -> Yf temporarily (k x k, ld ldf), rd -> rd compacted
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    int r = t / k, c = t % k;
+    Lf[r * ldf + c] = Hf[idx[r] * ldf + idx[c]];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    int r = t / k, c = t % k;
+    Hf[r * ldf + c] = Mf[idx[r] * ldf + idx[c]];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float tmp[MAXS];
+    for (int r = 0; r < k; ++r) tmp[r] = rd[idx[r]];
+    for (int r = 0; r < k; ++r) rd[r] = tmp[r];
+  }
+  __syncthreads();
+  RR_MARK(3);
+  // 3. M = L^-1 G^_B L^-T: Y = L^-1 G^_B in Hf (column-parallel), then M = L^-1 Y^T into Mf
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    for (int r = 0; r < k; ++r) {
+      float v = Hf[r * ldf + c];
+      for (int s = 0; s < r; ++s) v -= Lf[r * ldf + s] * Hf[s * ldf + c];
+      Hf[r * ldf + c] = v * rd[r];
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    for (int r = 0; r < k; ++r) {
+      float v = Hf[c * ldf + r];
+      for (int s = 0; s < r; ++s) v -= Lf[r * ldf + s] * Mf[s * ldf + c];
+      Mf[r * ldf + c] = v * rd[r];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    int r = t / k, c = t % k;
+    float v = (r == c) ? Mf[r * ldf + c] : 0.5f * (Mf[r * ldf + c] + Mf[c * ldf + r]);
+    Hf[r * ldf + c] = v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) Mf[(t / k) * ldf + t % k] = Hf[(t / k) * ldf + t % k];
+  __syncthreads();
+  RR_MARK(4);
+  // 4. Householder tridiagonalisation of Hf (k x k): T = Q^T M Q
+  for (int j = 0; j + 2 < k; ++j) {
+    const int len = k - j - 1;
+    if (wid == 0) {
+      float s2 = 0.f;
+      for (int i = lane; i < len; i += 32) { float x = Hf[(j + 1 + i) * ldf + j]; s2 += x * x; }
+      for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      if (lane == 0) {
+        float x0 = Hf[(j + 1) * ldf + j];
+        float tail = s2 - x0 * x0;
+        if (!(tail > 1e-30f * s2) || s2 == 0.f) {
+          ht[j] = 0.f;
+          te[j] = x0;
+        } else {
+          float alpha = -copysignf(sqrtf(s2), x0);
+          float v0 = x0 - alpha;
+          Hf[(j + 1) * ldf + j] = v0;
+          ht[j] = 2.f / (tail + v0 * v0);
+          te[j] = alpha;
+        }
+        td[j] = Hf[j * ldf + j];
+      }
+    }
+    __syncthreads();
+    const float tj = ht[j];
+    if (tj != 0.f) {
+      // p = tau * A22 v
+      for (int r = threadIdx.x; r < len; r += blockDim.x) {
+        const float* row = Hf + (j + 1 + r) * ldf + (j + 1);
+        float s0 = 0.f, s1 = 0.f;
+        int c = 0;
+        for (; c + 1 < len; c += 2) {
+          s0 += row[c] * Hf[(j + 1 + c) * ldf + j];
+          s1 += row[c + 1] * Hf[(j + 2 + c) * ldf + j];
+        }
+        if (c < len) s0 += row[c] * Hf[(j + 1 + c) * ldf + j];
+        pv[r] = tj * (s0 + s1);
+      }
+      __syncthreads();
+      if (wid == 0) {
+        float s = 0.f;
+        for (int i = lane; i < len; i += 32) s += pv[i] * Hf[(j + 1 + i) * ldf + j];
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) sh_f[0] = 0.5f * tj * s;
+      }
+      __syncthreads();
+      const float K = sh_f[0];
+      for (int r = threadIdx.x; r < len; r += blockDim.x) wv[r] = pv[r] - K * Hf[(j + 1 + r) * ldf + j];
+      __syncthreads();
+      for (int t = threadIdx.x; t < len * len; t += blockDim.x) {
+        int r = t / len, c = t % len;
+        float vr = Hf[(j + 1 + r) * ldf + j], vc = Hf[(j + 1 + c) * ldf + j];
+        Hf[(j + 1 + r) * ldf + (j + 1 + c)] -= vr * wv[c] + wv[r] * vc;
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (k >= 2) {
+      td[k - 2] = Hf[(k - 2) * ldf + (k - 2)];
+      te[k - 2] = Hf[(k - 1) * ldf + (k - 2)];
+      if (k >= 3) {}  // ht[k-2] unused
+    }
+    td[k - 1] = Hf[(k - 1) * ldf + (k - 1)];
+    for (int i = 0; i + 1 < k; ++i) te2[i] = te[i] * te[i];
+  }
+  __syncthreads();
+  RR_MARK(5);
+  // 5. the M largest eigenvalues of T by multisection bisection (one warp per eigenvalue)
+  {
+    float glo = 3.4e38f, ghi = -3.4e38f, emax = 0.f;
+    for (int i = 0; i < k; ++i) {
+      float r = (i > 0 ? fabsf(te[i - 1]) : 0.f) + (i + 1 < k ? fabsf(te[i]) : 0.f);
+      glo = fminf(glo, td[i] - r);
+      ghi = fmaxf(ghi, td[i] + r);
+      emax = fmaxf(emax, fabsf(td[i]) + r);
+    }
+    const float pivmin = fmaxf(1e-30f, 1e-37f * emax * emax);
+    const float width = fmaxf(ghi - glo, 1e-30f);
+    glo -= 2e-6f * width + pivmin;
+    ghi += 2e-6f * width + pivmin;
+    for (int q = wid; q < M; q += nw) {
+      const int target = k - 1 - q;           // ascending index of the q-th largest
+      float lo = glo, hi = ghi;
+      for (int round = 0; round < 10; ++round) {
+        float step = (hi - lo) / 33.f;
+        float x = lo + step * (float)(lane + 1);
+        int c = sturm_count(td, te2, k, x, pivmin);
+        unsigned above = __ballot_sync(0xffffffffu, c > target);
+        float nlo = lo, nhi = hi;
+        if (above) {
+          int f = __ffs(above) - 1;
+          nhi = __shfl_sync(0xffffffffu, x, f);
+          if (f > 0) nlo = __shfl_sync(0xffffffffu, x, f - 1);
+        } else {
+          nlo = __shfl_sync(0xffffffffu, x, 31);
+        }
+        lo = nlo; hi = nhi;
+        if (hi - lo <= 1.2e-7f * fmaxf(fabsf(lo), fabsf(hi))) break;
+      }
+      if (lane == 0) mu[q] = 0.5f * (lo + hi);
+    }
+  }
+  __syncthreads();
+  RR_MARK(6);
+  // 6. inverse iteration on T - mu I (tridiagonal LU with partial pivoting), one thread per vector
+  for (int q = threadIdx.x; q < M; q += blockDim.x) {
+    float* u0 = scr + (size_t)q * 6 * k;
+    float* u1 = u0 + k;
+    float* u2 = u1 + k;
+    float* lm = u2 + k;
+    float* y = lm + k;
+    int* pv_ = reinterpret_cast<int*>(y + k);
+    float nrmT = 0.f;
+    for (int i = 0; i < k; ++i) nrmT = fmaxf(nrmT, fabsf(td[i]) + (i > 0 ? fabsf(te[i - 1]) : 0.f) + (i + 1 < k ? fabsf(te[i]) : 0.f));
+    const float tiny = fmaxf(nrmT * 1.2e-7f, 1e-30f);
+    const float lam = mu[q];
+    float p = td[0] - lam, qq = (k > 1) ? te[0] : 0.f;
+    for (int i = 0; i + 1 < k; ++i) {
+      float c = te[i], an = td[i + 1] - lam, bn = (i + 2 < k) ? te[i + 1] : 0.f;
+      if (fabsf(c) > fabsf(p)) {
+        float l = p / c;
+        u0[i] = c; u1[i] = an; u2[i] = bn; lm[i] = l; pv_[i] = 1;
+        p = qq - l * an; qq = -l * bn;
+      } else {
+        if (fabsf(p) < tiny) p = copysignf(tiny, p == 0.f ? 1.f : p);
+        float l = c / p;
+        u0[i] = p; u1[i] = qq; u2[i] = 0.f; lm[i] = l; pv_[i] = 0;
+        p = an - l * qq; qq = bn;
+      }
+    }
+    if (fabsf(p) < tiny) p = copysignf(tiny, p == 0.f ? 1.f : p);
+    u0[k - 1] = p;
+    // starting vector: deterministic, not orthogonal to any eigenvector in practice
+    for (int i = 0; i < k; ++i) y[i] = 1.f + 0.37f * __sinf(1.3f * i + 0.7f * q);
+    for (int itn = 0; itn < 3; ++itn) {
+      for (int i = 0; i + 1 < k; ++i) {
+        if (pv_[i]) { float t = y[i]; y[i] = y[i + 1]; y[i + 1] = t; }
+        y[i + 1] -= lm[i] * y[i];
+      }
+      for (int i = k - 1; i >= 0; --i) {
+        float v = y[i];
+        if (i + 1 < k) v -= u1[i] * y[i + 1];
+        if (i + 2 < k) v -= u2[i] * y[i + 2];
+        y[i] = v / u0[i];
+      }
+      float s = 0.f;
+      for (int i = 0; i < k; ++i) s = fmaxf(s, fabsf(y[i]));
+      float inv = s > 0.f ? 1.f / s : 1.f;
+      for (int i = 0; i < k; ++i) y[i] *= inv;
+    }
+    for (int i = 0; i < k; ++i) Yf[i * MAXM + q] = y[i];
+  }
+  __syncthreads();
+  RR_MARK(7);
+  // 7. CGS2 over the M vectors (in order of decreasing mu), then unit norm
+  for (int j = 0; j < M; ++j) {
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i = wid; i < j; i += nw) {
+        float s = 0.f;
+        for (int r = lane; r < k; r += 32) s += Yf[r * MAXM + i] * Yf[r * MAXM + j];
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) dots[i] = s;
+      }
+      __syncthreads();
+      for (int r = threadIdx.x; r < k; r += blockDim.x) {
+        float v = Yf[r * MAXM + j];
+        for (int i = 0; i < j; ++i) v -= dots[i] * Yf[r * MAXM + i];
+        Yf[r * MAXM + j] = v;
+      }
+      __syncthreads();
+    }
+    if (wid == 0) {
+      float s = 0.f;
+      for (int r = lane; r < k; r += 32) { float v = Yf[r * MAXM + j]; s += v * v; }
+      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) sh_f[1] = s > 0.f ? rsqrtf(s) : 0.f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < k; r += blockDim.x) Yf[r * MAXM + j] *= sh_f[1];
+    __syncthreads();
+  }
+  RR_MARK(8);
+  // 8. back-transform y <- Q y (Householder reflectors in reverse), one warp per vector
+  for (int q = wid; q < M; q += nw) {
+    for (int j = k - 3; j >= 0; --j) {
+      const float tj = ht[j];
+      if (tj == 0.f) continue;
+      float s = 0.f;
+      for (int r = j + 1 + lane; r < k; r += 32) s += Hf[r * ldf + j] * Yf[r * MAXM + q];
+      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      s *= tj;
+      for (int r = j + 1 + lane; r < k; r += 32) Yf[r * MAXM + q] -= s * Hf[r * ldf + j];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  RR_MARK(9);
+  // 9. Ritz values and coefficients: theta = 1/mu, c = D L^-T y / sqrt(mu) (then c^T G_B c = 1)
+  if (threadIdx.x == 0) {
+    int b = 0;
+    for (int q = 0; q < M; ++q) if (!(mu[q] > 0.f) || !isfinite(mu[q])) b = 1;
+    bad = b;
+  }
+  __syncthreads();
+  if (bad) {
+    if (threadIdx.x == 0) { a.st->done = DONE_ERROR; a.st->err = MGE_ENOTFINITE; a.st->bad_stage = 4; }
+    return;
+  }
+  Small* sm = a.sm;
+  for (int t = threadIdx.x; t < n * M; t += blockDim.x) { sm->Cx[(t / M) * MAXM + t % M] = 0.0; sm->Cp[(t / M) * MAXM + t % M] = 0.0; }
+  // z = L^-T y (k x M, leading dimension M) in Hf; the reflectors are no longer needed
+  float* Z = Hf;
+  float* U = scr;   // k x M, leading dimension M; the inverse-iteration scratch is free
+  __syncthreads();
+  for (int q = threadIdx.x; q < M; q += blockDim.x) {
+    for (int r = k - 1; r >= 0; --r) {
+      float v = Yf[r * MAXM + q];
+      for (int s = r + 1; s < k; ++s) v -= Lf[s * ldf + r] * Z[s * M + q];
+      Z[r * M + q] = v * rd[r];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < k * M; t += blockDim.x) {
+    int r = t / M, q = t % M;
+    double s = (double)rsqrtf(mu[q]);
+    sm->Cx[idx[r] * MAXM + q] = dsc[idx[r]] * (double)Z[r * M + q] * s;
+  }
+  for (int q = threadIdx.x; q < M; q += blockDim.x) sm->lam[q] = 1.0 / (double)mu[q];
+  RR_MARK(10);
+  // 10. C_p.  In u = L^T z coordinates the G_B inner product is u^T M u', and a Ritz vector
+  //     is u = y / sqrt(mu) with M y = mu y, so M-orthogonality to it is Euclidean
+  //     orthogonality to y.
+  if (nx > 0) {
+    __syncthreads();
+    // z_p: the W/P rows of z (X rows zeroed), in place
+    for (int t = threadIdx.x; t < k * M; t += blockDim.x) {
+      int r = t / M;
+      if (idx[r] < nx) Z[t] = 0.f;
+    }
+    __syncthreads();
+    // u = L^T z_p
+    for (int t = threadIdx.x; t < k * M; t += blockDim.x) {
+      int r = t / M, q = t % M;
+      float v = 0.f;
+      for (int s_ = r; s_ < k; ++s_) v += Lf[s_ * ldf + r] * Z[s_ * M + q];
+      U[r * M + q] = v;
+    }
+    __syncthreads();
+    // u <- u - Y (Y^T u)
+    for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
+      int i = t / M, q = t % M;
+      float v = 0.f;
+      for (int r = 0; r < k; ++r) v += Yf[r * MAXM + i] * U[r * M + q];
+      gp[i * MAXM + q] = v;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < k * M; t += blockDim.x) {
+      int r = t / M, q = t % M;
+      float v = U[r * M + q];
+      for (int i = 0; i < M; ++i) v -= Yf[r * MAXM + i] * gp[i * MAXM + q];
+      U[r * M + q] = v;
+    }
+    __syncthreads();
+    // Gram u^T M u -> Cholesky with dropping -> u <- u L_p^-T
+    for (int t = threadIdx.x; t < k * M; t += blockDim.x) {
+      int r = t / M, q = t % M;
+      float v = 0.f;
+      for (int c = 0; c < k; ++c) v += Mf[r * ldf + c] * U[c * M + q];
+      Z[r * M + q] = v;       // M u
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
+      int i = t / M, q = t % M;
+      float v = 0.f;
+      for (int r = 0; r < k; ++r) v += U[r * M + i] * Z[r * M + q];
+      gp[i * MAXM + q] = v;
+    }
+    for (int i = threadIdx.x; i < M; i += blockDim.x) { pkeep[i] = 1; taup[i] = (float)a.tau_p; }
+    __syncthreads();
+    for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
+      int i = t / M, q = t % M;
+      if (i < q) { float v = 0.5f * (gp[i * MAXM + q] + gp[q * MAXM + i]); gp[i * MAXM + q] = v; gp[q * MAXM + i] = v; }
+    }
+    __syncthreads();
+    chol_drop<float>(gp, MAXM, M, taup, pkeep, rdp);
+    for (int r = threadIdx.x; r < k; r += blockDim.x) {
+      for (int c = 0; c < M; ++c) {
+        float v = U[r * M + c];
+        if (rdp[c] > 0.f) {
+          for (int s_ = 0; s_ < c; ++s_) v -= U[r * M + s_] * gp[c * MAXM + s_];
+          U[r * M + c] = v * rdp[c];
+        } else {
+          U[r * M + c] = 0.f;
+        }
+      }
+    }
+    __syncthreads();
+    // z_p = L^-T u into Z, C_p = D z_p
+    for (int q = threadIdx.x; q < M; q += blockDim.x) {
+      for (int r = k - 1; r >= 0; --r) {
+        float v = U[r * M + q];
+        for (int s_ = r + 1; s_ < k; ++s_) v -= Lf[s_ * ldf + r] * Z[s_ * M + q];
+        Z[r * M + q] = v * rd[r];
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < k * M; t += blockDim.x) {
+      int r = t / M, q = t % M;
+      sm->Cp[idx[r] * MAXM + q] = dsc[idx[r]] * (double)Z[r * M + q];
+    }
+  }
+  __syncthreads();
+  if (a.is_double) store_coeffs<double, float>(a);
+  else store_coeffs<float, float>(a);
+  if (threadIdx.x == 0) a.st->kept = k;
+  RR_MARK(11);
+#undef RR_MARK
+}
+
+// ---------------------------------------------------------------------------------------
+// FP64 form: Cholesky of G^_B with dropping, standard form, cyclic two-sided Jacobi
+// ---------------------------------------------------------------------------------------
+__device__ int jacobi_eig(double* A, double* V, int ld, int k) {
+  __shared__ int rotated;
+  __shared__ double cs_c[MAXS / 2 + 1], cs_s[MAXS / 2 + 1];
+  __shared__ int pr_p[MAXS / 2 + 1], pr_q[MAXS / 2 + 1];
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) V[(t / k) * ld + t % k] = (t / k == t % k) ? 1.0 : 0.0;
+  const int kk = k + (k & 1);
+  const int np = kk / 2;
+  int sweeps = 0;
+  __syncthreads();
+  if (k < 2) return 0;
+  for (; sweeps < 60; ++sweeps) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int s = 0; s < kk - 1; ++s) {
+      if (threadIdx.x < np) {
+        int i = threadIdx.x;
+        int p, q;
+        if (i == 0) { p = kk - 1; q = s; }
+        else { p = (s + i) % (kk - 1); q = (s - i + kk - 1) % (kk - 1); }
+        if (p > q) { int t = p; p = q; q = t; }
+        double c = 1.0, sn = 0.0;
+        if (q < k) {
+          double app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
+          if (apq != 0.0 && fabs(apq) > 1e-17 * sqrt(fabs(app * aqq))) {
+            double theta = (aqq - app) / (2.0 * apq);
+            double t;
+            if (fabs(theta) > 1e150) t = 0.5 / theta;
+            else t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            sn = t * c;
+            rotated = 1;
+          }
+        }
+        pr_p[i] = p; pr_q[i] = q; cs_c[i] = c; cs_s[i] = sn;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < np * k; t += blockDim.x) {
+        int i = t / k, j = t % k;
+        double s_ = cs_s[i];
+        if (s_ == 0.0) continue;
+        double c = cs_c[i];
+        int p = pr_p[i], q = pr_q[i];
+        double ap = A[p * ld + j], aq = A[q * ld + j];
+        A[p * ld + j] = c * ap - s_ * aq;
+        A[q * ld + j] = s_ * ap + c * aq;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < np * k; t += blockDim.x) {
+        int i = t / k, j = t % k;
+        double s_ = cs_s[i];
+        if (s_ == 0.0) continue;
+        double c = cs_c[i];
+        int p = pr_p[i], q = pr_q[i];
+        double ap = A[j * ld + p], aq = A[j * ld + q];
+        A[j * ld + p] = c * ap - s_ * aq;
+        A[j * ld + q] = s_ * ap + c * aq;
+        double vp = V[j * ld + p], vq = V[j * ld + q];
+        V[j * ld + p] = c * vp - s_ * vq;
+        V[j * ld + q] = s_ * vp + c * vq;
+      }
+      __syncthreads();
+    }
+    int r = rotated;
+    __syncthreads();
+    if (!r) break;
+  }
+  return sweeps;
+}
+
+__global__ void __launch_bounds__(kThreads) k_rr_jacobi(RRArgs a) {
+  if (a.st->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M = a.M, n = a.nb * a.M, nx = a.nx;
+  const int ld = n + 1;
+  double* bufA = reinterpret_cast<double*>(smem_raw);
+  double* bufB = bufA + n * ld;
+  double* bufC = bufB + n * ld;
+  double* bufV = bufC + n * ld;
+  __shared__ double dsc[MAXS], tau[MAXS], theta[MAXS], rdb[MAXS];
+  __shared__ int keep[MAXS], idx[MAXS], order[MAXS], pkeep[MAXM];
+  __shared__ int kcount;
+  Small* sm = a.sm;
+  if (!load_grams(a, bufA, bufB, n, ld)) {
+    if (threadIdx.x == 0) { a.st->done = DONE_ERROR; a.st->err = MGE_ENOTFINITE; a.st->bad_stage = 1; }
+    return;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double d = bufB[i * ld + i];
+    bool live = d > 0.0 && isfinite(d);
+    dsc[i] = live ? 1.0 / sqrt(d) : 0.0;
+    keep[i] = live ? 1 : 0;
+    tau[i] = a.tau;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int i = t / n, j = t % n;
+    double s = dsc[i] * dsc[j];
+    bufA[i * ld + j] *= s;
+    bufB[i * ld + j] *= s;
+  }
+  __syncthreads();
+  chol_drop<double>(bufB, ld, n, tau, keep, rdb);
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int i = 0; i < n; ++i) if (keep[i]) idx[c++] = i;
+    kcount = c;
+  }
+  __syncthreads();
+  const int k = kcount;
+  if (k < M) {
+    if (threadIdx.x == 0) { a.st->done = DONE_ERROR; a.st->err = MGE_ECHOLESKY; a.st->kept = k; }
+    return;
+  }
+  if (threadIdx.x == 0 && k < n) atomicAdd(&a.st->drops, 1);
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    int r = t / k, c = t % k;
+    bufC[r * ld + c] = bufA[idx[r] * ld + idx[c]];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    int r = t / k, c = t % k;
+    bufA[r * ld + c] = bufB[idx[r] * ld + idx[c]];
+  }
+  __syncthreads();
+  double* Lk = bufA;
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    for (int r = 0; r < k; ++r) {
+      double v = bufC[r * ld + c];
+      for (int s = 0; s < r; ++s) v -= Lk[r * ld + s] * bufC[s * ld + c];
+      bufC[r * ld + c] = v / Lk[r * ld + r];
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    for (int r = 0; r < k; ++r) {
+      double v = bufC[c * ld + r];
+      for (int s = 0; s < r; ++s) v -= Lk[r * ld + s] * bufB[s * ld + c];
+      bufB[r * ld + c] = v / Lk[r * ld + r];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    int r = t / k, c = t % k;
+    if (c > r) {
+      double v = 0.5 * (bufB[r * ld + c] + bufB[c * ld + r]);
+      bufB[r * ld + c] = v;
+      bufB[c * ld + r] = v;
+    }
+  }
+  __syncthreads();
+  jacobi_eig(bufB, bufV, ld, k);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) theta[i] = bufB[i * ld + i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    int rank = 0;
+    double ti = theta[i];
+    for (int j = 0; j < k; ++j) {
+      double tj = theta[j];
+      if (tj < ti || (tj == ti && j < i)) ++rank;
+    }
+    order[rank] = i;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < M; c += blockDim.x) {
+    int e = order[c];
+    for (int r = k - 1; r >= 0; --r) {
+      double v = bufV[r * ld + e];
+      for (int s = r + 1; s < k; ++s) v -= Lk[s * ld + r] * bufC[s * ld + c];
+      bufC[r * ld + c] = v / Lk[r * ld + r];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * M; t += blockDim.x) { sm->Cx[(t / M) * MAXM + t % M] = 0.0; sm->Cp[(t / M) * MAXM + t % M] = 0.0; }
+  __syncthreads();
+  for (int t = threadIdx.x; t < k * M; t += blockDim.x) {
+    int r = t / M, c = t % M;
+    sm->Cx[idx[r] * MAXM + c] = dsc[idx[r]] * bufC[r * ld + c];
+  }
+  for (int c = threadIdx.x; c < M; c += blockDim.x) sm->lam[c] = theta[order[c]];
+  if (nx > 0) {
+    double* U = bufB;
+    double* Z = bufC;
+    __syncthreads();
+    for (int t = threadIdx.x; t < k * M; t += blockDim.x) {
+      int r = t / M, c = t % M;
+      double v = 0.0;
+      for (int s = r; s < k; ++s)
+        if (idx[s] >= nx) v += Lk[s * ld + r] * Z[s * ld + c];
+      U[r * ld + c] = v;
+    }
+    double* Gc = bufC + M;
+    __syncthreads();
+    for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
+      int i = t / M, c = t % M;
+      double v = 0.0;
+      int e = order[i];
+      for (int r = 0; r < k; ++r) v += bufV[r * ld + e] * U[r * ld + c];
+      Gc[i * ld + c] = v;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < k * M; t += blockDim.x) {
+      int r = t / M, c = t % M;
+      double v = U[r * ld + c];
+      for (int i = 0; i < M; ++i) v -= bufV[r * ld + order[i]] * Gc[i * ld + c];
+      U[r * ld + c] = v;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
+      int i = t / M, c = t % M;
+      double v = 0.0;
+      for (int r = 0; r < k; ++r) v += U[r * ld + i] * U[r * ld + c];
+      Gc[i * ld + c] = v;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < M; i += blockDim.x) { pkeep[i] = 1; tau[i] = a.tau_p; }
+    __syncthreads();
+    chol_drop<double>(Gc, ld, M, tau, pkeep, rdb);
+    for (int r = threadIdx.x; r < k; r += blockDim.x) {
+      for (int c = 0; c < M; ++c) {
+        double v = U[r * ld + c];
+        double lcc = Gc[c * ld + c];
+        if (lcc > 0.0) {
+          for (int s = 0; s < c; ++s) v -= U[r * ld + s] * Gc[c * ld + s];
+          U[r * ld + c] = v / lcc;
+        } else {
+          U[r * ld + c] = 0.0;
+        }
+      }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < M; c += blockDim.x) {
+      for (int r = k - 1; r >= 0; --r) {
+        double v = U[r * ld + c];
+        for (int s = r + 1; s < k; ++s) v -= Lk[s * ld + r] * Z[s * ld + c];
+        Z[r * ld + c] = v / Lk[r * ld + r];
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < k * M; t += blockDim.x) {
+      int r = t / M, c = t % M;
+      sm->Cp[idx[r] * MAXM + c] = dsc[idx[r]] * Z[r * ld + c];
+    }
+  }
+  __syncthreads();
+  if (a.is_double) store_coeffs<double, double>(a);
+  else store_coeffs<float, double>(a);
+  if (threadIdx.x == 0) a.st->kept = k;
+}
+
+// ---------------------------------------------------------------------------------------
+// wprep: backward errors and convergence; projections Mx, Mp and the normalisation of the
+// projected W_raw (Cholesky with dropping, in R precision)
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_wprep(WprepArgs a) {
+  if (a.st->done) return;
+  const int M = a.M;
+  Small* sm = a.sm;
+  __shared__ double G2[MAXS * MAXM];
+  __shared__ double cs[MAXM];
+  __shared__ R G[MAXM * (MAXM + 1)];
+  __shared__ R tau[MAXM], rdw[MAXM];
+  __shared__ int keep[MAXM];
+  __shared__ int conv_all, bad, bad_g;
+  const int ld = M + 1;
+  const int rows = (a.has_x ? M : 0) + (a.has_p ? M : 0) + M;
+  long long clk0 = clock64();
+  if (threadIdx.x == 0) { conv_all = 1; bad = 0; bad_g = 0; }
+  // sum the W-side Gram partials and the column sums
+  for (int t = threadIdx.x; t < rows * M; t += blockDim.x) {
+    int i = t / M, j = t % M;
+    G2[i * MAXM + j] = sum_strided(&sm->partW[0][i * MAXM + j], a.ncl_w, MAXS * MAXM);
+  }
+  for (int t = threadIdx.x; t < M; t += blockDim.x) {
+    cs[t] = a.deflate ? sum_strided(&sm->partC[0][t], a.ncl_w, MAXM) : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) a.st->wp_clk[0] = clock64() - clk0;
+  if (a.check) {
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+      double rn2 = sum_strided(&sm->partN[0][k], a.ncl_n, 2 * MAXM);
+      double xn2 = sum_strided(&sm->partN[0][MAXM + k], a.ncl_n, 2 * MAXM);
+      double lam = sm->lam[k];
+      double eta = sqrt(rn2) / ((a.norm + fabs(lam) * a.bmax) * sqrt(xn2));
+      if (!isfinite(eta) || !isfinite(lam)) bad = 1;
+      a.st->eta[k] = eta;
+      a.st->lambda[k] = lam;
+      if (k < a.K && !(eta <= a.tol)) conv_all = 0;
+    }
+  }
+  __syncthreads();
+  if (a.check && threadIdx.x == 0) {
+    a.st->iter += 1;
+    if (bad) { a.st->done = DONE_ERROR; a.st->err = MGE_ENOTFINITE; a.st->bad_stage = 2; }
+    else if (conv_all) a.st->done = DONE_CONVERGED;
+    else if (a.st->iter >= a.maxiter) a.st->done = DONE_MAXITER;
+  }
+  const int ox = 0, op = a.has_x ? M : 0, ow = (a.has_x ? M : 0) + (a.has_p ? M : 0);
+  const double inv_n = 1.0 / (double)a.n;
+  for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
+    int i = t / M, j = t % M;
+    // R-precision subtraction: entries below tau_w * G_jj are dropped anyway
+    R g = (R)(0.5 * (G2[(ow + i) * MAXM + j] + G2[(ow + j) * MAXM + i]));
+    for (int l = 0; l < M; ++l) {
+      if (a.has_x) g -= (R)G2[(ox + l) * MAXM + i] * (R)G2[(ox + l) * MAXM + j];
+      if (a.has_p) g -= (R)G2[(op + l) * MAXM + i] * (R)G2[(op + l) * MAXM + j];
+    }
+    if (a.deflate) g -= (R)(cs[i] * cs[j] * inv_n);
+    G[i * ld + j] = g;
+    if (!isfinite((double)g)) bad_g = 1;
+  }
+  for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
+    int i = t / M, j = t % M;
+    sm->Mx[i * MAXM + j] = a.has_x ? G2[(ox + i) * MAXM + j] : 0.0;
+    sm->Mp[i * MAXM + j] = a.has_p ? G2[(op + i) * MAXM + j] : 0.0;
+  }
+  for (int t = threadIdx.x; t < M; t += blockDim.x) {
+    double g0 = G2[(ow + t) * MAXM + t];
+    tau[t] = (R)(a.tau_w * g0);
+    keep[t] = (g0 > 0.0 && isfinite(g0)) ? 1 : 0;
+    sm->cmean[t] = cs[t] * inv_n;
+  }
+  __syncthreads();
+  if (bad_g) {
+    if (threadIdx.x == 0) { a.st->done = DONE_ERROR; a.st->err = MGE_ENOTFINITE; a.st->bad_stage = 3; }
+    return;
+  }
+  if (threadIdx.x == 0) a.st->wp_clk[1] = clock64() - clk0;
+  chol_drop<R>(G, ld, M, tau, keep, rdw);
+  if (threadIdx.x == 0) a.st->wp_clk[2] = clock64() - clk0;
+  // Linv = L^-T (upper triangular); column c solves L^T y = e_c
+  for (int c = threadIdx.x; c < M; c += blockDim.x) {
+    R y[MAXM];
+    for (int r = M - 1; r >= 0; --r) {
+      if (!(rdw[r] > R(0))) { y[r] = R(0); continue; }
+      R v = (r == c) ? R(1) : R(0);
+      for (int s = r + 1; s < M; ++s) v -= G[s * ld + r] * y[s];
+      y[r] = v * rdw[r];
+    }
+    for (int r = 0; r < M; ++r) sm->Linv[r * MAXM + c] = (double)y[r];
+  }
+  __syncthreads();
+  if (a.is_double) {
+    SmallT<double>* o = static_cast<SmallT<double>*>(a.smt);
+    for (int t = threadIdx.x; t < MAXM * MAXM; t += blockDim.x) { o->Linv[t] = sm->Linv[t]; o->Mx[t] = sm->Mx[t]; o->Mp[t] = sm->Mp[t]; }
+    for (int t = threadIdx.x; t < MAXM; t += blockDim.x) o->cmean[t] = sm->cmean[t];
+  } else {
+    SmallT<float>* o = static_cast<SmallT<float>*>(a.smt);
+    for (int t = threadIdx.x; t < MAXM * MAXM; t += blockDim.x) { o->Linv[t] = (float)sm->Linv[t]; o->Mx[t] = (float)sm->Mx[t]; o->Mp[t] = (float)sm->Mp[t]; }
+    for (int t = threadIdx.x; t < MAXM; t += blockDim.x) o->cmean[t] = (float)sm->cmean[t];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) a.st->wp_clk[3] = clock64() - clk0;
+}
+
+// ---------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------
+size_t rr_inv_smem(int n) {
+  size_t d = 2 * (size_t)n * (n + 1) * sizeof(double);
+  size_t f = 3 * (size_t)n * (n + 1) * sizeof(float) + (size_t)n * MAXM * sizeof(float) +
+             (size_t)MAXM * 6 * n * sizeof(float);
+  return d + f;
+}
+size_t rr_jacobi_smem(int n) { return 4 * (size_t)n * (n + 1) * sizeof(double); }
+
+cudaError_t rr_configure() {
+  cudaError_t e = cudaFuncSetAttribute(k_rr_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_inv_smem(MAXS));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_rr_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_jacobi_smem(MAXS));
+}
+
+void launch_rr(cudaStream_t st, const RRArgs& a, bool inverse_form) {
+  int n = a.nb * a.M;
+  if (inverse_form) k_rr_inv<<<1, kRRThreads, rr_inv_smem(n), st>>>(a);
+  else k_rr_jacobi<<<1, kThreads, rr_jacobi_smem(n), st>>>(a);
+}
+
+void launch_wprep(cudaStream_t st, const WprepArgs& a, bool fp64) {
+  if (fp64) k_wprep<double><<<1, kThreads, 0, st>>>(a);
+  else k_wprep<float><<<1, kThreads, 0, st>>>(a);
+}
+
+}  // namespace lob
+}  // namespace mge

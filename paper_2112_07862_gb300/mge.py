@@ -1,0 +1,332 @@
+"""Python binding of libmge (include/mge.h): argument marshalling only.
+
+Every function named ``mge_*`` here calls the C entry point of the same name; the
+arithmetic runs in the library's CUDA kernels.  Host arrays are numpy arrays; device
+arrays are torch CUDA tensors (their ``data_ptr()`` is passed).  Loading fails loudly when
+libmge.so is missing: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmge.so")
+
+MGE_OK, MGE_EINVAL, MGE_ENOTSYM, MGE_EISOLATED, MGE_EDEGENERATE, MGE_ENOTCONVERGED = 0, 1, 2, 3, 4, 5
+MGE_ENOMEM, MGE_EAGAIN, MGE_ETIMEOUT, MGE_EDEVICE, MGE_ECHOLESKY, MGE_ENOTFOUND = 6, 7, 8, 9, 10, 11
+MGE_ENOTFINITE = 12
+MGE_FP64, MGE_FP32, MGE_BF16 = 0, 1, 2
+PRECISION = {"fp64": MGE_FP64, "fp32": MGE_FP32, "bf16": MGE_BF16}
+
+# every symbol include/mge.h declares
+EXPORTS = [
+    "mge_create", "mge_destroy", "mge_strerror", "mge_ctx_last_error", "mge_ctx_stats",
+    "mge_ctx_set_timing", "mge_ctx_reset_stats", "mge_build_graph_ops", "mge_ops_destroy",
+    "mge_ops_info", "mge_ops_export", "mge_ops_apply", "mge_embed", "mge_submit", "mge_poll",
+    "mge_release",
+]
+
+
+class mge_stats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_uint64), ("spmm_launches", C.c_uint64),
+                ("spmm_ms", C.c_double), ("spmm_bytes", C.c_uint64), ("hbm_in_use", C.c_size_t)]
+
+
+class mge_ops_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("eps_override_set", C.c_int), ("eps_override", C.c_double),
+                ("mu_override_set", C.c_int), ("mu_override", C.c_double), ("eps_tol", C.c_double),
+                ("eps_guard", C.c_int), ("eps_maxiter", C.c_int), ("seed", C.c_uint64),
+                ("stream", C.c_void_p)]
+
+
+class mge_ops_info_t(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz_w", C.c_int64), ("nnz_a", C.c_int64), ("nnz_q", C.c_int64),
+                ("eps", C.c_double), ("mu", C.c_double), ("norm_a", C.c_double), ("bmax", C.c_double),
+                ("degenerate", C.c_int), ("two_hop_components", C.c_int), ("eps_iters", C.c_int),
+                ("eps_resid", C.c_double), ("build_ms", C.c_double)]
+
+
+class mge_embed_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("guard", C.c_int), ("maxiter", C.c_int), ("seed", C.c_uint64),
+                ("check_every", C.c_int), ("use_graph", C.c_int), ("x0", C.c_void_p), ("x0_cols", C.c_int),
+                ("x0_on_device", C.c_int), ("v_on_device", C.c_int), ("stream", C.c_void_p)]
+
+
+class mge_embed_info(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("m", C.c_int), ("drops", C.c_int),
+                ("resid", C.c_double * 64), ("solve_ms", C.c_double)]
+
+
+class mge_request(C.Structure):
+    _fields_ = [("n", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("w", C.c_void_p),
+                ("K", C.c_int), ("tol", C.c_double), ("precision", C.c_int), ("guard", C.c_int),
+                ("maxiter", C.c_int), ("seed", C.c_uint64)]
+
+
+class mge_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("n", C.c_int64), ("K", C.c_int), ("eps", C.c_double),
+                ("mu", C.c_double), ("iters", C.c_int), ("latency_ms", C.c_double),
+                ("queue_ms", C.c_double), ("lambda_", C.POINTER(C.c_double)), ("V", C.POINTER(C.c_double))]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libmge.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2112_07862_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, i, i64, d, u64, sz = C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_uint64, C.c_size_t
+    sig = {
+        "mge_create": (i, [i, sz, C.POINTER(vp)]),
+        "mge_destroy": (i, [vp]),
+        "mge_strerror": (C.c_char_p, [i]),
+        "mge_ctx_last_error": (C.c_char_p, [vp]),
+        "mge_ctx_stats": (i, [vp, C.POINTER(mge_stats)]),
+        "mge_ctx_set_timing": (i, [vp, i]),
+        "mge_ctx_reset_stats": (i, [vp]),
+        "mge_build_graph_ops": (i, [vp, i64, vp, vp, vp, i, C.POINTER(mge_ops_opts), C.POINTER(vp)]),
+        "mge_ops_destroy": (i, [vp]),
+        "mge_ops_info": (i, [vp, C.POINTER(mge_ops_info_t)]),
+        "mge_ops_export": (i, [vp, vp, vp, vp, vp, vp, vp, vp, vp, i]),
+        "mge_ops_apply": (i, [vp, vp, i, i, i, vp, vp, vp]),
+        "mge_embed": (i, [vp, vp, i, d, C.POINTER(mge_embed_opts), vp, vp, C.POINTER(mge_embed_info)]),
+        "mge_submit": (i, [vp, C.POINTER(mge_request), C.POINTER(u64)]),
+        "mge_poll": (i, [vp, u64, i, C.POINTER(mge_result)]),
+        "mge_release": (i, [vp, u64]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class MgeError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def _ptr(a):
+    """Host numpy array or torch tensor -> address (None passes NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+# ---- one wrapper per C entry point ------------------------------------------------------
+
+def mge_strerror(s: int) -> str:
+    return load().mge_strerror(s).decode()
+
+
+def mge_create(device: int = 0, hbm_budget_bytes: int = 0):
+    h = C.c_void_p()
+    s = load().mge_create(device, hbm_budget_bytes, C.byref(h))
+    if s != MGE_OK:
+        raise MgeError(s, f"mge_create: {mge_strerror(s)}")
+    return h
+
+
+def mge_destroy(ctx) -> int:
+    return load().mge_destroy(ctx)
+
+
+def mge_ctx_last_error(ctx) -> str:
+    return load().mge_ctx_last_error(ctx).decode()
+
+
+def mge_ctx_stats(ctx) -> mge_stats:
+    st = mge_stats()
+    load().mge_ctx_stats(ctx, C.byref(st))
+    return st
+
+
+def mge_ctx_set_timing(ctx, on: bool) -> int:
+    return load().mge_ctx_set_timing(ctx, 1 if on else 0)
+
+
+def mge_ctx_reset_stats(ctx) -> int:
+    return load().mge_ctx_reset_stats(ctx)
+
+
+def _check(ctx, s, what, ok=(MGE_OK,)):
+    if s not in ok:
+        raise MgeError(s, f"{what}: {mge_strerror(s)}: {mge_ctx_last_error(ctx)}")
+    return s
+
+
+def mge_build_graph_ops(ctx, n, row_ptr, col, w, on_device: bool = False, opts: mge_ops_opts | None = None):
+    """Returns (ops handle, status).  Host inputs are numpy int64/int32/float64 arrays; device
+    inputs are torch tensors of the same dtypes."""
+    h = C.c_void_p()
+    if not on_device:
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+    s = load().mge_build_graph_ops(ctx, int(n), _ptr(row_ptr), _ptr(col), _ptr(w), 1 if on_device else 0,
+                                   C.byref(opts) if opts is not None else None, C.byref(h))
+    _check(ctx, s, "mge_build_graph_ops", ok=(MGE_OK, MGE_EDEGENERATE))
+    return h, s
+
+
+def mge_ops_destroy(ops) -> int:
+    return load().mge_ops_destroy(ops)
+
+
+def mge_ops_info(ops) -> mge_ops_info_t:
+    info = mge_ops_info_t()
+    load().mge_ops_info(ops, C.byref(info))
+    return info
+
+
+def mge_ops_export(ops):
+    """Host copies of A, Q (CSR, FP64), b and T as numpy arrays."""
+    info = mge_ops_info(ops)
+    n, na, nq = info.n, info.nnz_a, info.nnz_q
+    a_ptr = np.empty(n + 1, np.int64); a_col = np.empty(na, np.int32); a_val = np.empty(na, np.float64)
+    q_ptr = np.empty(n + 1, np.int64); q_col = np.empty(nq, np.int32); q_val = np.empty(nq, np.float64)
+    b = np.empty(n, np.float64); T = np.empty(n, np.int32)
+    s = load().mge_ops_export(ops, _ptr(a_ptr), _ptr(a_col), _ptr(a_val), _ptr(q_ptr), _ptr(q_col),
+                              _ptr(q_val), _ptr(b), _ptr(T), 0)
+    if s != MGE_OK:
+        raise MgeError(s, "mge_ops_export")
+    return dict(a_ptr=a_ptr, a_col=a_col, a_val=a_val, q_ptr=q_ptr, q_col=q_col, q_val=q_val, b=b, T=T)
+
+
+def mge_ops_apply(ctx, ops, which: int, precision: int, m: int, X, Y, stream=None) -> int:
+    """Y = A X (which=0) or Q X (which=1); X, Y torch CUDA tensors [n, m] row-major."""
+    s = load().mge_ops_apply(ctx, ops, which, precision, m, _ptr(X), _ptr(Y), stream)
+    return _check(ctx, s, "mge_ops_apply")
+
+
+def mge_embed(ctx, ops, K: int, tol: float, opts: mge_embed_opts | None = None, V=None):
+    """Returns (lambda[K] numpy, V, info, status).  V: a host numpy float64 array [K, n]
+    (column-major n x K) or a device tensor when opts.v_on_device; allocated on the host
+    when None."""
+    info = mge_ops_info(ops)
+    lam = np.empty(K, np.float64)
+    if V is None and not (opts is not None and opts.v_on_device):
+        V = np.empty((K, info.n), np.float64)
+    ei = mge_embed_info()
+    s = load().mge_embed(ctx, ops, K, float(tol), C.byref(opts) if opts is not None else None,
+                         _ptr(lam), _ptr(V), C.byref(ei))
+    _check(ctx, s, "mge_embed", ok=(MGE_OK, MGE_ENOTCONVERGED))
+    return lam, V, ei, s
+
+
+def mge_submit(ctx, req: mge_request) -> int:
+    t = C.c_uint64()
+    s = load().mge_submit(ctx, C.byref(req), C.byref(t))
+    _check(ctx, s, "mge_submit")
+    return t.value
+
+
+def mge_poll(ctx, ticket: int, timeout_ms: int = -1):
+    r = mge_result()
+    s = load().mge_poll(ctx, ticket, timeout_ms, C.byref(r))
+    return s, r
+
+
+def mge_release(ctx, ticket: int) -> int:
+    return load().mge_release(ctx, ticket)
+
+
+# ---- conveniences ------------------------------------------------------------------------
+
+def ops_opts(precision="fp32", eps=None, mu=None, eps_tol=0.0, seed=0, stream=None, eps_guard=0,
+             eps_maxiter=0) -> mge_ops_opts:
+    o = mge_ops_opts()
+    o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    if eps is not None:
+        o.eps_override_set, o.eps_override = 1, float(eps)
+    if mu is not None:
+        o.mu_override_set, o.mu_override = 1, float(mu)
+    o.eps_tol = eps_tol
+    o.eps_guard = eps_guard
+    o.eps_maxiter = eps_maxiter
+    o.seed = seed
+    o.stream = stream
+    return o
+
+
+def embed_opts(precision="fp32", guard=0, maxiter=0, seed=0, check_every=0, use_graph=True, x0=None,
+               v_on_device=False, stream=None) -> mge_embed_opts:
+    o = mge_embed_opts()
+    o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    o.guard = guard
+    o.maxiter = maxiter
+    o.seed = seed
+    o.check_every = check_every
+    o.use_graph = 1 if use_graph else 0
+    if x0 is not None:
+        o.x0 = _ptr(x0)
+        o.x0_cols = x0.shape[0]
+        o.x0_on_device = 1 if hasattr(x0, "data_ptr") else 0
+    o.v_on_device = 1 if v_on_device else 0
+    o.stream = stream
+    return o
+
+
+class Context:
+    """Owns an mge_ctx; closes it on exit."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.h = mge_create(device, hbm_budget_bytes)
+
+    def close(self):
+        if self.h:
+            mge_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def build(self, g, **kw):
+        """Operators for a manifold_graphs.Graph-like object (n, row_ptr, col, w) on the host."""
+        ops, s = mge_build_graph_ops(self.h, g.n, g.row_ptr, g.col, g.w, False, ops_opts(**kw))
+        return Ops(ops, s)
+
+    def embed(self, ops, K, tol, **kw):
+        lam, V, info, s = mge_embed(self.h, ops.h, K, tol, embed_opts(**kw))
+        return lam, V.T if isinstance(V, np.ndarray) else V, info, s
+
+    def stats(self):
+        return mge_ctx_stats(self.h)
+
+
+class Ops:
+    def __init__(self, h, status):
+        self.h = h
+        self.status = status
+
+    def info(self):
+        return mge_ops_info(self.h)
+
+    def export(self):
+        return mge_ops_export(self.h)
+
+    def close(self):
+        if self.h:
+            mge_ops_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
