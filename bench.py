@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Benchmark of the embedding hot path on GB300.
+
+One step = the whole hot path on one seeded synthetic manifold graph: the operator build
+(two-hop CSR assembly, Q, eps = lambda_2(Q) by LOBPCG, mu, A, B; Sec. 4) and the LOBPCG
+solve for the first K generalized eigenpairs of (A, B) (Sec. 4.3).  The graph (the kNN
+construction of Sec. 5.1, seeded points on a 3-D swiss roll) is input preparation and is
+not timed.
+
+Default workload: N = 200,000 points on a swiss roll, symmetric 10-NN graph with Gaussian
+weights, K = 8, backward-error tolerance 1e-5, FP32 blocks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank embeds its own graph (seed + rank,
+same size): independent problems, no collective on the data path ("scaling": "weak").
+The reference arm (--impl reference) times the CPU oracle on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "node-embeddings/s (K=8 generalized eigenvectors per node, backward error <= 1e-5)"
+UNIT = "node-embeddings/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=200_000)
+    p.add_argument("--shape", default="swiss_roll")
+    p.add_argument("--knn", type=int, default=10)
+    p.add_argument("--K", type=int, default=8)
+    p.add_argument("--tol", type=float, default=1e-5)
+    p.add_argument("--precision", default="fp32")
+    p.add_argument("--seed", type=int, default=2)
+    p.add_argument("--cpu-sample-n", type=int, default=10_000)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload(a, n=None):
+    return {"workload": f"{a.shape} N={n or a.n} {a.knn}-NN K={a.K} tol={a.tol:g} {a.precision} blocks",
+            "shape": a.shape, "n": n or a.n, "knn": a.knn, "K": a.K, "tol": a.tol,
+            "precision": a.precision, "seed": a.seed}
+
+
+# ---------------------------------------------------------------------------------------
+# distributed plumbing (barrier and max-over-ranks only; no data-path collective)
+# ---------------------------------------------------------------------------------------
+class Dist:
+    def __init__(self, backend):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            if self.pg.get_backend() == "nccl":
+                import torch
+                self.pg.barrier(device_ids=[torch.cuda.current_device()])
+            else:
+                self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        busy = [s for s in sm if mx is None or s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------------------
+def spmm_traffic_per_launch():
+    """DRAM bytes per SpMM launch from the committed ncu summary, if the kernel source it was
+    taken from is unchanged; otherwise null."""
+    path = os.path.join(ROOT, "profiles", "spmm_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        src = open(os.path.join(ROOT, "paper_2112_07862_gb300", "csrc", "lobpcg.cu"), "rb").read()
+        if d.get("source_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return d.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def run_ours(a, dist):
+    import numpy as np
+    import torch
+
+    import manifold_graphs as mg
+    from paper_2112_07862_gb300 import mge
+
+    torch.cuda.set_device(dist.local)
+    g = mg.manifold_graph(a.shape, a.n, a.knn, a.seed + dist.rank)
+    ctx = mge.Context(dist.local)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    # device-resident inputs for the kernel-level number
+    rp_d = torch.from_numpy(g.row_ptr).cuda()
+    col_d = torch.from_numpy(g.col).cuda()
+    w_d = torch.from_numpy(g.w).cuda()
+    V_d = torch.empty((a.K, g.n), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
+    oo = mge.ops_opts(a.precision, stream=sptr)
+    eo = mge.embed_opts(a.precision, v_on_device=True, stream=sptr)
+    status = {"build": None, "embed": None}
+
+    def step():
+        flush.zero_()
+        h, s = mge.mge_build_graph_ops(ctx.h, g.n, rp_d, col_d, w_d, True, oo)
+        lam, V, info, s2 = mge.mge_embed(ctx.h, h, a.K, a.tol, eo, V_d)
+        mge.mge_ops_destroy(h)
+        status["build"], status["embed"] = s, s2
+        return lam, info
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    mge.mge_ctx_reset_stats(ctx.h)
+    mge.mge_ctx_set_timing(ctx.h, True)
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters = []
+    for _ in range(a.steps):
+        lam, info = step()
+        iters.append(info.iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    mge.mge_ctx_set_timing(ctx.h, False)
+    st = mge.mge_ctx_stats(ctx.h)
+    ms = e0.elapsed_time(e1)
+    ms_max = dist.max(ms)
+    per_step = ms_max / a.steps
+    value = dist.world * g.n * a.steps / (ms_max / 1e3)
+
+    # end to end through the public API with host buffers: H2D of W inside the call, V back
+    e2e = None
+    if not a.no_e2e:
+        rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+        col_h = torch.from_numpy(g.col).pin_memory()
+        w_h = torch.from_numpy(g.w).pin_memory()
+        V_h = torch.empty((a.K, g.n), dtype=torch.float64).pin_memory()
+        oo_h = mge.ops_opts(a.precision, stream=sptr)
+        eo_h = mge.embed_opts(a.precision, v_on_device=False, stream=sptr)
+
+        def step_e2e():
+            flush.zero_()
+            h, s = mge.mge_build_graph_ops(ctx.h, g.n, rp_h.numpy(), col_h.numpy(), w_h.numpy(), False, oo_h)
+            lam, V, info, s2 = mge.mge_embed(ctx.h, h, a.K, a.tol, eo_h, V_h.numpy())
+            mge.mge_ops_destroy(h)
+            return lam
+
+        step_e2e()
+        torch.cuda.synchronize()
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            step_e2e()
+        torch.cuda.synchronize()
+        t_e2e = dist.max(time.perf_counter() - t0)
+        e2e = {"value": dist.world * g.n * a.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes + g.w.nbytes),
+               "d2h_bytes_per_step": int(V_h.numel() * 8 + a.K * 8),
+               "ms_per_step": 1e3 * t_e2e / a.steps}
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "of measured"
+    if not hbm:
+        hbm, peak_src = 6800.0, "of fallback"
+    achieved = (st.spmm_bytes / (st.spmm_ms / 1e3) / 1e9) if st.spmm_ms > 0 else None
+    traffic = spmm_traffic_per_launch()
+    roofline = {"kernel": "k_spmm_w (SpMM of A with the fused W projection/normalisation)",
+                "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved / hbm) if achieved else None, "peak_source": peak_src,
+                "traffic": traffic, "launches_timed": st.spmm_launches,
+                "avg_launch_us": 1e3 * st.spmm_ms / st.spmm_launches if st.spmm_launches else None,
+                "algorithmic_bytes_per_launch": st.spmm_bytes / st.spmm_launches if st.spmm_launches else None}
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if a.precision == "fp32" else a.precision.replace("fp", "f"),
+        "data": "synthetic: seeded swiss-roll points, exact symmetric kNN graph, Gaussian weights",
+        "config": dict(workload(a), l2="flushed (256 MB write) before every step",
+                       parallelism=f"replicas x{dist.world} (independent graphs, no collective)"),
+        "gpu_launches": int(st.kernel_launches),
+        "lobpcg_iters_per_step": statistics.mean(iters),
+        "status": {"build": status["build"], "embed": status["embed"]},
+        "roofline": roofline,
+        "e2e": e2e,
+        "clocks": clk,
+    }
+    ctx.close()
+    return res
+
+
+# ---------------------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------------------
+def oracle_step(a, n, seed):
+    import manifold_graphs as mg
+    from oracle import eigen as oe
+    from oracle import graph_ops as og
+    g = mg.manifold_graph(a.shape, n, a.knn, seed)
+    t0 = time.perf_counter()
+    ops = og.from_graph(g, eps_tol=1e-7)
+    r = oe.lobpcg(ops.A, ops.b, a.K, tol=a.tol, seed=seed)
+    dt = time.perf_counter() - t0
+    return dt, r
+
+
+def cpu_baseline(a, n, steps=1):
+    times = [oracle_step(a, n, a.seed)[0] for _ in range(steps)]
+    t = min(times)
+    return {"value": n / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{a.shape} N={n} {a.knn}-NN K={a.K} tol={a.tol:g}: whole oracle pipeline (FP64 "
+                      f"operator build incl. eps by LOBPCG, then FP64 LOBPCG), {t:.2f} s per graph"}
+
+
+def run_reference(a, dist):
+    if dist.rank != 0:
+        return None
+    n = a.cpu_sample_n
+    for _ in range(a.warmup):
+        oracle_step(a, n, a.seed)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        oracle_step(a, n, a.seed)
+    t = time.perf_counter() - t0
+    v = n * a.steps / t
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": dist.world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(workload(a), sample=f"N={n} per step (bounded sample of the workload)"),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{a.shape} N={n} per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        dist = Dist("gloo")
+        res = run_reference(a, dist)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        dist.close()
+        return
+    dist = Dist("nccl")
+    res = run_ours(a, dist)
+    if dist.rank == 0:
+        if dist.world == 1 and not a.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline(a, a.cpu_sample_n)
+        print(json.dumps(res), flush=True)
+    dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -17,7 +17,9 @@
  *   - Pointers flagged "host or device" are device pointers when the matching on_device
  *     flag is nonzero, host pointers otherwise.  Device pointers must belong to the
  *     context's device.  Caller buffers stay caller-owned; the library never frees them.
- *   - Handles (mge_ctx, mge_ops) are library-owned and freed by their destroy call.
+ *   - Handles (mge_ctx, mge_ops) are library-owned and freed by their destroy call.  An ops
+ *     handle may outlive its context: after mge_destroy it can still be exported and must
+ *     still be passed to mge_ops_destroy, which releases its device memory.
  *   - A context is used by one host thread at a time, except mge_submit/mge_poll/
  *     mge_release, which are thread-safe.
  *   - Streams are passed as void* (a cudaStream_t); NULL selects the context's stream.
@@ -58,8 +60,13 @@ typedef enum {
 } mge_status;
 
 /* Arithmetic of the iterated blocks X, W, P and of the stored matrix values.
- * Gram accumulation is FP32 (FP64 in MGE_FP64); the Rayleigh-Ritz eigensolve, the
- * Cholesky factorisations and the residual-norm test are FP64 in every precision. */
+ *   MGE_FP64  everything in FP64, including the Rayleigh-Ritz eigensolve (cyclic Jacobi).
+ *   MGE_FP32  FP32 blocks and SpMM; Gram sums in FP32 with compensation, reduced across
+ *             the GPU in FP64; residual norms and backward errors in FP64; the
+ *             Rayleigh-Ritz scaling in FP64 and its eigensolve in FP32 on the inverse
+ *             pencil (the wanted smallest eigenvalues become the largest, which FP32
+ *             resolves to relative accuracy).
+ *   MGE_BF16  reserved (rejected with MGE_EINVAL by this build). */
 typedef enum { MGE_FP64 = 0, MGE_FP32 = 1, MGE_BF16 = 2 } mge_precision;
 
 typedef struct mge_ctx mge_ctx;

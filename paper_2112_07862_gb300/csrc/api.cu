@@ -96,14 +96,24 @@ mge_status mge_create(int device, size_t hbm_budget_bytes, mge_ctx** out) {
   return MGE_OK;
 }
 
+// The context's host object lives until the last ops handle built from it is destroyed, so
+// an ops handle may outlive mge_destroy (its device memory is released by mge_ops_destroy).
+static void ctx_release(Ctx* ctx) {
+  if (--ctx->refs == 0) delete static_cast<mge_ctx*>(ctx->self);
+}
+
 mge_status mge_destroy(mge_ctx* c) {
   if (!c) return MGE_EINVAL;
   Ctx* ctx = &c->impl;
+  if (ctx->closed) return MGE_EINVAL;
+  ctx->closed = true;
   cudaSetDevice(ctx->device);
   serve_shutdown(ctx);
   for (auto& e : ctx->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+  ctx->ev_pool.clear();
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
-  delete c;
+  ctx->stream = nullptr;
+  ctx_release(ctx);
   return MGE_OK;
 }
 
@@ -145,10 +155,13 @@ mge_status mge_build_graph_ops(mge_ctx* c, int64_t n, const int64_t* row_ptr, co
   Ctx* ctx = &c->impl;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return MGE_EDEVICE;
   cudaStream_t st = pick_stream(ctx, opts ? opts->stream : nullptr);
+  if (ctx->closed) return MGE_EINVAL;
   mge_ops* o = new mge_ops();
+  ctx->refs++;
   mge_status s = build_graph_ops_impl(ctx, st, n, row_ptr, col, w, on_device, opts, &o->impl);
   if (s != MGE_OK && s != MGE_EDEGENERATE) {
     delete o;
+    ctx_release(ctx);
     return s;
   }
   *out = o;
@@ -157,7 +170,10 @@ mge_status mge_build_graph_ops(mge_ctx* c, int64_t n, const int64_t* row_ptr, co
 
 mge_status mge_ops_destroy(mge_ops* o) {
   if (!o) return MGE_EINVAL;
+  Ctx* ctx = o->impl.ctx;
+  if (ctx) cudaSetDevice(ctx->device);
   delete o;
+  if (ctx) ctx_release(ctx);
   return MGE_OK;
 }
 
@@ -178,7 +194,7 @@ mge_status mge_ops_export(const mge_ops* o, int64_t* a_ptr, int32_t* a_col, doub
   Ctx* ctx = op.ctx;
   cudaSetDevice(ctx->device);
   cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  cudaStream_t st = ctx->stream;
+  cudaStream_t st = ctx->closed ? nullptr : ctx->stream;
   if (a_ptr) MGE_CUDA(ctx, cudaMemcpyAsync(a_ptr, op.a_ptr.p, (op.n + 1) * sizeof(int64_t), k, st));
   if (a_col && op.nnz_a) MGE_CUDA(ctx, cudaMemcpyAsync(a_col, op.a_col.p, op.nnz_a * sizeof(int32_t), k, st));
   if (a_val && op.nnz_a) MGE_CUDA(ctx, cudaMemcpyAsync(a_val, op.a_val.p, op.nnz_a * sizeof(double), k, st));
@@ -215,6 +231,7 @@ static LobOp make_op(const Ops& op, int which, int precision) {
 mge_status mge_ops_apply(mge_ctx* c, const mge_ops* o, int which, int precision, int m, const void* X, void* Y,
                          void* stream) {
   if (!c || !o || !X || !Y || (which != 0 && which != 1)) return MGE_EINVAL;
+  if (c->impl.closed) return MGE_EINVAL;
   Ctx* ctx = &c->impl;
   cudaSetDevice(ctx->device);
   if (precision != MGE_FP64 && precision != MGE_FP32) {
@@ -232,6 +249,7 @@ mge_status mge_ops_apply(mge_ctx* c, const mge_ops* o, int which, int precision,
 mge_status mge_embed(mge_ctx* c, const mge_ops* o, int K, double tol, const mge_embed_opts* opts,
                      double* lambda, void* V, mge_embed_info* info) {
   if (!c || !o || !lambda) return MGE_EINVAL;
+  if (c->impl.closed) return MGE_EINVAL;
   Ctx* ctx = &c->impl;
   cudaSetDevice(ctx->device);
   mge_embed_opts e{};

@@ -669,11 +669,20 @@ struct Solver {
       e1 = ctx->ev_pool[ctx->ev_used].second;
       ctx->ev_used++;
       ctx->ev_bytes.push_back(spmm_bytes(hx, hp));
-      MGE_CUDA(ctx, cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal));
+    }
+    // inside a stream capture the records become external event nodes of the graph
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (timed) {
+      MGE_CUDA(ctx, cudaStreamIsCapturing(st, &cap));
+      if (cap == cudaStreamCaptureStatusActive) MGE_CUDA(ctx, cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal));
+      else MGE_CUDA(ctx, cudaEventRecord(e0, st));
     }
     k_spmm_w<T, M><<<grid_rows, kThreads, 0, st>>>(s);
     MGE_LAUNCHED(ctx, 1);
-    if (timed) MGE_CUDA(ctx, cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal));
+    if (timed) {
+      if (cap == cudaStreamCaptureStatusActive) MGE_CUDA(ctx, cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal));
+      else MGE_CUDA(ctx, cudaEventRecord(e1, st));
+    }
     return MGE_OK;
   }
 

@@ -62,6 +62,8 @@ struct Ctx {
   int num_sms = 0;
   void* serve = nullptr;           // serving state (serve.cu)
   void* self = nullptr;            // the owning mge_ctx*
+  std::atomic<int> refs{1};        // the context itself plus one per live ops handle
+  bool closed = false;
 };
 
 mge_status dev_alloc(Ctx* ctx, void** p, size_t bytes);

@@ -1,0 +1,79 @@
+"""Serving: requests admitted by HBM footprint run concurrently; each result is the same as
+when the request runs alone (eigenvalues to 1e-10 relative, vectors to 1e-8)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import manifold_graphs as mg
+
+pytestmark = pytest.mark.gpu
+
+
+def request(mge, g, K, tol=1e-6, seed=0, precision="fp32", guard=4):
+    r = mge.mge_request()
+    r.n = g.n
+    r.row_ptr = g.row_ptr.ctypes.data
+    r.col = g.col.ctypes.data
+    r.w = g.w.ctypes.data
+    r.K = K
+    r.tol = tol
+    r.precision = mge.PRECISION[precision]
+    r.guard = guard
+    r.maxiter = 0
+    r.seed = seed
+    return r
+
+
+def test_results_are_the_same_alone_and_in_the_mix(gpu_lib):
+    mge = gpu_lib
+    graphs = [(mg.manifold_graph("square", 3000, 8, 1), 4), (mg.manifold_graph("sphere", 5000, 10, 2), 8),
+              (mg.manifold_graph("swiss_roll", 8000, 10, 3), 8), (mg.manifold_graph("torus", 2000, 12, 4), 2),
+              (mg.manifold_graph("square", 12000, 10, 5), 16), (mg.manifold_graph("sphere", 1500, 10, 6), 4)]
+    with mge.Context(0) as ctx:
+        alone = []
+        for g, K in graphs:
+            ops = ctx.build(g, precision="fp32")
+            lam, V, info, s = ctx.embed(ops, K, 1e-6, precision="fp32", guard=4)
+            alone.append((lam, V))
+            ops.close()
+    with mge.Context(0) as ctx:
+        tickets = [mge.mge_submit(ctx.h, request(mge, g, K)) for g, K in graphs]
+        for (g, K), t, (lam0, V0) in zip(graphs, tickets, alone):
+            s, r = mge.mge_poll(ctx.h, t, -1)
+            assert s == 0 and r.status == 0, (s, r.status)
+            lam = np.ctypeslib.as_array(r.lambda_, shape=(K,)).copy()
+            V = np.ctypeslib.as_array(r.V, shape=(K, g.n)).T.copy()
+            assert np.allclose(lam, lam0, rtol=1e-10, atol=0)
+            assert np.max(np.abs(V - V0)) < 1e-8
+            assert r.latency_ms >= r.queue_ms >= 0
+            assert mge.mge_release(ctx.h, t) == 0
+
+
+def test_poll_and_release_errors(gpu_lib):
+    mge = gpu_lib
+    with mge.Context(0) as ctx:
+        s, r = mge.mge_poll(ctx.h, 12345, 0)
+        assert s == mge.MGE_ENOTFOUND
+        assert mge.mge_release(ctx.h, 999) == mge.MGE_ENOTFOUND
+
+
+def test_budget_admission_rejects_oversized_request(gpu_lib):
+    mge = gpu_lib
+    g = mg.manifold_graph("square", 20000, 10, 9)
+    with mge.Context(0, hbm_budget_bytes=1 << 20) as ctx:
+        with pytest.raises(mge.MgeError) as e:
+            mge.mge_submit(ctx.h, request(mge, g, 8))
+        assert e.value.status == mge.MGE_ENOMEM
+
+
+def test_budget_serialises_but_completes(gpu_lib):
+    """A budget that fits one request at a time still serves them all, in order."""
+    mge = gpu_lib
+    gs = [mg.manifold_graph("square", 4000, 8, s) for s in range(4)]
+    with mge.Context(0, hbm_budget_bytes=64 << 20) as ctx:
+        ts = [mge.mge_submit(ctx.h, request(mge, g, 4)) for g in gs]
+        for t in ts:
+            s, r = mge.mge_poll(ctx.h, t, -1)
+            assert s == 0 and r.status == 0
+            mge.mge_release(ctx.h, t)
