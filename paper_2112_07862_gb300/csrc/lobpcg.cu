@@ -52,9 +52,10 @@ struct SpmmArgs {
 // gathers in flight per warp.
 template <int M> struct SpmmShape {
   static constexpr int G = M / 4;
-  static constexpr int S = (G == 1) ? 8 : (G == 2) ? 4 : (G <= 4) ? (8 / G > 0 ? 8 / G : 1) : 1;
+  static constexpr int S = (G == 1) ? 16 : (G == 2) ? 8 : (G <= 4) ? 4 : 2;
   static constexpr int TEAM = G * S;
   static constexpr int RPW = 32 / TEAM;
+  static constexpr int BATCH = 4;     // nonzeros per lane whose index loads precede their gathers
 };
 
 template <typename T, int M>
@@ -88,24 +89,26 @@ __global__ void __launch_bounds__(kThreads) k_spmm_w(SpmmArgs<T> a) {
     if (valid) {
       ldg4(a.Wr + row * M + c0, wi);
       const int64_t pe = a.ptr[row + 1];
-      int64_t p = a.ptr[row] + sub;
-      // two nonzeros per step: both gathers are issued before either is consumed
-      for (; p + S < pe; p += 2 * S) {
-        const int32_t j0 = __ldg(a.col + p), j1 = __ldg(a.col + p + S);
-        const T v0 = __ldg(a.val + p), v1 = __ldg(a.val + p + S);
-        T w0[4], w1[4];
-        ldg4(a.Wr + (int64_t)j0 * M + c0, w0);
-        ldg4(a.Wr + (int64_t)j1 * M + c0, w1);
+      constexpr int BT = Sh::BATCH;
+      // BATCH nonzeros per lane at a time: their index and value loads are all issued, then
+      // their gathers; an empty slot gathers the row itself with value 0
+      for (int64_t p0 = a.ptr[row] + sub; p0 < pe; p0 += (int64_t)BT * S) {
+        int32_t j[BT];
+        T v[BT];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] += v0 * (w0[q] - wi[q]) + v1 * (w1[q] - wi[q]);
-      }
-      if (p < pe) {
-        const int32_t j0 = __ldg(a.col + p);
-        const T v0 = __ldg(a.val + p);
-        T w0[4];
-        ldg4(a.Wr + (int64_t)j0 * M + c0, w0);
+        for (int b = 0; b < BT; ++b) {
+          const int64_t p = p0 + (int64_t)b * S;
+          const bool ok = p < pe;
+          j[b] = ok ? __ldg(a.col + p) : (int32_t)row;
+          v[b] = ok ? __ldg(a.val + p) : T(0);
+        }
+        T w[BT][4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] += v0 * (w0[q] - wi[q]);
+        for (int b = 0; b < BT; ++b) ldg4(a.Wr + (int64_t)j[b] * M + c0, w[b]);
+#pragma unroll
+        for (int b = 0; b < BT; ++b)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q] += v[b] * (w[b][q] - wi[q]);
       }
     }
     // combine the S nonzero slices: lanes of slice 0 end up with the row sums
@@ -213,6 +216,16 @@ struct GramArgs {
 
 constexpr int kTileRows = 32;
 
+// Neumaier's compensated step acc += x, the lost low part collected in cmp; all in the
+// accumulator's own precision (FP64 arithmetic would run at GB300's low FP64 rate)
+template <typename A>
+__device__ __forceinline__ void neumaier(A& acc, A& cmp, A x) {
+  const A s = acc + x;
+  const A aa = acc < A(0) ? -acc : acc, ax = x < A(0) ? -x : x;
+  cmp += (aa >= ax) ? (acc - s) + x : (x - s) + acc;
+  acc = s;
+}
+
 __device__ __forceinline__ void decode_item(int item, int nb1, int b1, int bl, bool sym2, int b2, int& prod,
                                             int& bi, int& bj) {
   if (item < nb1) {
@@ -235,11 +248,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads) k_gram(Gr
   if (a.st && a.st->done) return;
   using A = T;   // accumulate in the block precision (FP32 for FP32 blocks), compensated
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sL = reinterpret_cast<T*>(smem_raw);
-  const int wl = a.nl * M, w1 = a.n1 * M, w2 = a.sym2 ? 0 : a.n2 * M;
-  T* sR1 = sL + kTileRows * wl;
-  T* sR2 = sR1 + kTileRows * w1;
-  T* sb = sR2 + kTileRows * w2;
+  const int wl = a.nl * M, w1 = a.n1 * M, ws = a.sym2 ? 0 : a.n2 * M;
   const int bl = wl / 4, b1 = w1 / 4, b2 = (a.sym2 ? wl : a.n2 * M) / 4;
   const int nb1 = bl * b1;
   const int nb2 = a.sym2 ? bl * (bl + 1) / 2 : bl * b2;
@@ -251,99 +260,100 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads) k_gram(Gr
   const int rg = threadIdx.x / tpi;
   const int ti = threadIdx.x % tpi;
   const bool has_group = rg < rs;
+  // each item: a 4x4 block of one product; its two 4-wide column slices as row pointers
+  const T* lp[IPT];
+  const T* rp[IPT];
   int it_prod[IPT], it_i[IPT], it_j[IPT];
-  bool it_ok[IPT];
+  bool it_ok[IPT], it_w[IPT];
 #pragma unroll
   for (int u = 0; u < IPT; ++u) {
     int item = ti + u * tpi;
     it_ok[u] = has_group && item < nblk;
-    it_prod[u] = 0; it_i[u] = 0; it_j[u] = 0;
-    if (it_ok[u]) decode_item(item, nb1, b1, bl, a.sym2, b2, it_prod[u], it_i[u], it_j[u]);
+    it_prod[u] = 0; it_i[u] = 0; it_j[u] = 0; it_w[u] = false;
+    lp[u] = rp[u] = nullptr;
+    if (it_ok[u]) {
+      decode_item(item, nb1, b1, bl, a.sym2, b2, it_prod[u], it_i[u], it_j[u]);
+      const int ci = it_i[u] * 4, cj = it_j[u] * 4;
+      lp[u] = a.L[ci / M] + ci % M;
+      if (it_prod[u] == 1) rp[u] = a.R1[cj / M] + cj % M;
+      else if (a.sym2) { rp[u] = a.L[cj / M] + cj % M; it_w[u] = true; }
+      else { rp[u] = a.R2[cj / M] + cj % M; it_w[u] = true; }
+    }
   }
+  // this CTA's contiguous rows
+  const int64_t per = (a.n + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * per;
+  const int64_t r1 = min(a.n, r0 + per);
   A acc[IPT][16], cmp[IPT][16];
 #pragma unroll
   for (int u = 0; u < IPT; ++u)
 #pragma unroll
     for (int e = 0; e < 16; ++e) { acc[u][e] = A(0); cmp[u][e] = A(0); }
-  A cs = A(0);
-  const int ws = w2;
-  for (int64_t r0 = (int64_t)blockIdx.x * kTileRows; r0 < a.n; r0 += (int64_t)gridDim.x * kTileRows) {
-    const int nr = (int)((a.n - r0) < kTileRows ? (a.n - r0) : kTileRows);
-    __syncthreads();
-    for (int t = threadIdx.x; t < kTileRows * (wl / 4); t += kThreads) {
-      int r = t / (wl / 4), c = (t % (wl / 4)) * 4;
-      int blk = c / M, cc = c % M;
-      T v[4] = {0, 0, 0, 0};
-      if (r < nr) ldg4(a.L[blk] + (r0 + r) * M + cc, v);
+  constexpr int U = 4;                  // rows in flight per thread
+  constexpr int CHUNK = 16;             // row steps summed before the compensated fold
+  int steps = 0;
+  A at[IPT][16];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) sL[r * wl + c + q] = v[q];
-    }
-    for (int t = threadIdx.x; t < kTileRows * (w1 / 4); t += kThreads) {
-      int r = t / (w1 / 4), c = (t % (w1 / 4)) * 4;
-      int blk = c / M, cc = c % M;
-      T v[4] = {0, 0, 0, 0};
-      if (r < nr) ldg4(a.R1[blk] + (r0 + r) * M + cc, v);
+  for (int u = 0; u < IPT; ++u)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) sR1[r * w1 + c + q] = v[q];
-    }
-    for (int t = threadIdx.x; t < kTileRows * (ws / 4); t += kThreads) {
-      int r = t / (ws / 4), c = (t % (ws / 4)) * 4;
-      int blk = c / M, cc = c % M;
-      T v[4] = {0, 0, 0, 0};
-      if (r < nr) ldg4(a.R2[blk] + (r0 + r) * M + cc, v);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) sR2[r * ws + c + q] = v[q];
-    }
-    for (int t = threadIdx.x; t < kTileRows; t += kThreads)
-      sb[t] = (t < nr) ? (a.b ? a.b[r0 + t] : T(1)) : T(0);
-    __syncthreads();
-    if (a.csum && threadIdx.x < ws) {
-      A s = A(0);
-      for (int r = 0; r < nr; ++r) s += (A)sR2[r * ws + threadIdx.x];
-      cs += s;
-    }
+    for (int e = 0; e < 16; ++e) at[u][e] = A(0);
+  for (int64_t r = r0 + rg; r < r1; r += (int64_t)rs * U) {
 #pragma unroll
     for (int u = 0; u < IPT; ++u) {
       if (!it_ok[u]) continue;
-      A at[16];
+      T lv[U][4], rv[U][4], bw[U];
 #pragma unroll
-      for (int e = 0; e < 16; ++e) at[e] = A(0);
-      const T* lp = sL + it_i[u] * 4;
-      const T* rp;
-      int wr;
-      bool weighted = false;
-      if (it_prod[u] == 1) { rp = sR1 + it_j[u] * 4; wr = w1; }
-      else if (a.sym2) { rp = sL + it_j[u] * 4; wr = wl; weighted = true; }
-      else { rp = sR2 + it_j[u] * 4; wr = ws; weighted = true; }
-      for (int r = rg; r < kTileRows; r += rs) {
-        A lv[4], rv[4];
+      for (int k = 0; k < U; ++k) {
+        const int64_t rr = r + (int64_t)k * rs;
+        if (rr < r1) {
+          ldg4(lp[u] + rr * M, lv[k]);
+          ldg4(rp[u] + rr * M, rv[k]);
+          bw[k] = (it_w[u] && a.b) ? __ldg(a.b + rr) : T(1);
+        } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) { lv[q] = (A)lp[r * wl + q]; rv[q] = (A)rp[r * wr + q]; }
-        if (weighted) {
-          A bw = (A)sb[r];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) rv[q] *= bw;
+          for (int q = 0; q < 4; ++q) { lv[k][q] = T(0); rv[k][q] = T(0); }
+          bw[k] = T(0);
         }
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) at[p * 4 + q] += lv[p] * rv[q];
       }
-      // Neumaier-compensated add of the tile sum
 #pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        A s = acc[u][e] + at[e];
-        if (fabs((double)acc[u][e]) >= fabs((double)at[e])) cmp[u][e] += (acc[u][e] - s) + at[e];
-        else cmp[u][e] += (at[e] - s) + acc[u][e];
-        acc[u][e] = s;
-      }
+      for (int k = 0; k < U; ++k)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const A lb = (A)lv[k][p] * (A)bw[k];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) at[u][p * 4 + q] += lb * (A)rv[k][q];
+        }
+    }
+    if (++steps == CHUNK) {
+      steps = 0;
+#pragma unroll
+      for (int u = 0; u < IPT; ++u)
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          neumaier(acc[u][e], cmp[u][e], at[u][e]);
+          at[u][e] = A(0);
+        }
     }
   }
+#pragma unroll
+  for (int u = 0; u < IPT; ++u)
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      neumaier(acc[u][e], cmp[u][e], at[u][e]);
+    }
+  // column sums of R2 (deflation): thread c + ws*g sums rows g, g + ng, ... of column c
+  A cs = A(0);
+  const int ng = ws > 0 ? kThreads / ws : 0;
+  const int csg = ws > 0 ? threadIdx.x / ws : 0, csc = ws > 0 ? threadIdx.x % ws : 0;
+  if (a.csum && csg < ng) {
+    const T* src = a.R2[csc / M] + csc % M;
+    for (int64_t r = r0 + csg; r < r1; r += ng) cs += (A)__ldg(src + r * M);
+  }
   // CTA reduction: stage [rs][nblk][16], sum over row groups into FP64, then the cluster
-  __syncthreads();
   const int len = nblk * 16;
   A* stage = reinterpret_cast<A*>(smem_raw);
-  double* part = reinterpret_cast<double*>(smem_raw + (((size_t)rs * len * sizeof(A) + 15) / 16) * 16);
+  A* cstage = stage + (size_t)rs * len;
+  double* part = reinterpret_cast<double*>(smem_raw + ((((size_t)rs * len + kThreads) * sizeof(A) + 15) / 16) * 16);
 #pragma unroll
   for (int u = 0; u < IPT; ++u)
     if (it_ok[u]) {
@@ -351,22 +361,29 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads) k_gram(Gr
 #pragma unroll
       for (int e = 0; e < 16; ++e) stage[(size_t)rg * len + item * 16 + e] = acc[u][e] + cmp[u][e];
     }
+  if (a.csum) cstage[threadIdx.x] = (csg < ng) ? cs : A(0);
   __syncthreads();
   for (int t = threadIdx.x; t < len; t += kThreads) {
     double s = 0.0;
     for (int g = 0; g < rs; ++g) s += (double)stage[(size_t)g * len + t];
     part[t] = s;
   }
-  if (a.csum && threadIdx.x < ws) part[len + threadIdx.x] = (double)cs;
+  if (a.csum && threadIdx.x < ws) {
+    double s = 0.0;
+    for (int g = 0; g < ng; ++g) s += (double)cstage[g * ws + threadIdx.x];
+    part[len + threadIdx.x] = s;
+  }
   const int tot = len + (a.csum ? ws : 0);
   const int cl = cluster_id();
+  // each cluster adds its total into the single accumulator the consumer reads (and zeroes)
+  (void)cl;
   cluster_sum(part, tot, [&](int t, double v) {
-    if (t >= len) { a.csum[(size_t)cl * MAXM + (t - len)] = v; return; }
+    if (t >= len) { atomicAdd(a.csum + (t - len), v); return; }
     int item = t / 16, e = t % 16, p = e / 4, q = e % 4;
     int prod, bi, bj;
     decode_item(item, nb1, b1, bl, a.sym2, b2, prod, bi, bj);
-    if (prod == 1) a.out1[(size_t)cl * MAXS * MAXS + (bi * 4 + p) * MAXS + bj * 4 + q] = v;
-    else a.out2[(size_t)cl * a.stride2 + (bi * 4 + p) * a.ld2 + bj * 4 + q] = v;
+    if (prod == 1) atomicAdd(a.out1 + (bi * 4 + p) * MAXS + bj * 4 + q, v);
+    else atomicAdd(a.out2 + (bi * 4 + p) * a.ld2 + bj * 4 + q, v);
   });
 }
 
@@ -389,16 +406,16 @@ struct UpdArgs {
   const State* st;
 };
 
-template <typename T, int M>
+template <typename T, int M, int NB>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads) k_update(UpdArgs<T> a) {
   if (a.st->done) return;
   using A = T;
   constexpr int G = M / 4, RPW = 32 / G, NW = kThreads / 32;
-  __shared__ T sCx[MAXS * M], sCp[MAXS * M], sLam[M];
-  __shared__ A red[NW][32][8];
+  constexpr int NS = NB * M;
+  __shared__ T sCx[NS * M], sCp[NS * M], sLam[M];
+  __shared__ A red[NW][2 * M];
   __shared__ double part[2 * M];
-  const int ns = a.nb * M;
-  for (int t = threadIdx.x; t < ns * M; t += kThreads) {
+  for (int t = threadIdx.x; t < NS * M; t += kThreads) {
     int r = t / M, c = t % M;
     sCx[t] = a.smt->Cx[r * MAXM + c];
     sCp[t] = a.smt->Cp[r * MAXM + c];
@@ -414,28 +431,36 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads) k_update(
     const int64_t row = base + team;
     const bool valid = lane_ok && row < a.n;
     T x[4] = {0, 0, 0, 0}, ax[4] = {0, 0, 0, 0}, p[4] = {0, 0, 0, 0}, ap[4] = {0, 0, 0, 0};
+    T bi = T(1), di = T(0);
     if (valid) {
-      for (int blk = 0; blk < a.nb; ++blk) {
-        const T* sp = a.S[blk] + row * M;
-        const T* asp = a.AS[blk] + row * M;
+      bi = a.b ? a.b[row] : T(1);
+      di = a.dinv[row];
+      // PB blocks of the row are loaded before their first use (all of them when they fit)
+      constexpr int PB = (NB * M <= 48) ? NB : 1;
 #pragma unroll
-        for (int l = 0; l < M; l += 4) {
-          T sv[4], av[4];
-          ld4(sp + l, sv);
-          ld4(asp + l, av);
-          const int rbase = blk * M + l;
+      for (int b0 = 0; b0 < NB; b0 += PB) {
+        T sv[PB][M], av[PB][M];
 #pragma unroll
-          for (int t = 0; t < 4; ++t)
+        for (int k = 0; k < PB; ++k)
+#pragma unroll
+          for (int l = 0; l < M; l += 4) {
+            ld4(a.S[b0 + k] + row * M + l, &sv[k][l]);
+            ld4(a.AS[b0 + k] + row * M + l, &av[k][l]);
+          }
+#pragma unroll
+        for (int k = 0; k < PB; ++k)
+#pragma unroll
+          for (int l = 0; l < M; ++l) {
+            const int rr = (b0 + k) * M + l;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              T cx = sCx[(rbase + t) * M + c0 + q];
-              T cp = sCp[(rbase + t) * M + c0 + q];
-              x[q] += sv[t] * cx;
-              ax[q] += av[t] * cx;
-              p[q] += sv[t] * cp;
-              ap[q] += av[t] * cp;
+              const T cx = sCx[rr * M + c0 + q], cp = sCp[rr * M + c0 + q];
+              x[q] += sv[k][l] * cx;
+              ax[q] += av[k][l] * cx;
+              p[q] += sv[k][l] * cp;
+              ap[q] += av[k][l] * cp;
             }
-        }
+          }
       }
     }
     __syncwarp();   // every lane of the team has read the row before any lane overwrites it
@@ -446,8 +471,6 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads) k_update(
         st4(a.Po + row * M + c0, p);
         st4(a.APo + row * M + c0, ap);
       }
-      const T bi = a.b ? a.b[row] : T(1);
-      const T di = a.dinv[row];
       T r[4], w[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -460,25 +483,45 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads) k_update(
     }
     __syncwarp();
   }
-  // per-column sums: stage per lane, then thread c sums the lanes holding column c
+  // per-column sums: across the teams of a warp (lanes with equal tl), then across warps
+  if ((G & (G - 1)) == 0) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    red[wid][lane][q] = lane_ok ? pr[q] : A(0);
-    red[wid][lane][4 + q] = lane_ok ? px[q] : A(0);
+    for (int off = 16; off >= G; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        pr[q] += __shfl_xor_sync(0xffffffffu, pr[q], off);
+        px[q] += __shfl_xor_sync(0xffffffffu, px[q], off);
+      }
+    if (lane < G)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { red[wid][c0 + q] = pr[q]; red[wid][M + c0 + q] = px[q]; }
+  } else {
+    // team sizes of 3 or 6 lanes: lanes of the same column group sum through shared memory
+    __shared__ A lanes[NW][32][8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { lanes[wid][lane][q] = lane_ok ? pr[q] : A(0); lanes[wid][lane][4 + q] = lane_ok ? px[q] : A(0); }
+    __syncwarp();
+    if (lane < G) {
+      A sr[4] = {0, 0, 0, 0}, sx[4] = {0, 0, 0, 0};
+      for (int l = lane; l < RPW * G; l += G)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { sr[q] += lanes[wid][l][q]; sx[q] += lanes[wid][l][4 + q]; }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { red[wid][c0 + q] = sr[q]; red[wid][M + c0 + q] = sx[q]; }
+    }
   }
   __syncthreads();
   if (threadIdx.x < 2 * M) {
-    const int c = threadIdx.x % M, which = threadIdx.x / M;
-    const int ctl = c / 4, q = c % 4;
-    double s = 0.0;
-    for (int w = 0; w < NW; ++w)
-      for (int l = ctl; l < RPW * G; l += G) s += (double)red[w][l][which * 4 + q];
-    part[threadIdx.x] = s;
+    A s = A(0);
+#pragma unroll
+    for (int w = 0; w < NW; ++w) s += red[w][threadIdx.x];
+    part[threadIdx.x] = (double)s;
   }
   const int cl = cluster_id();
+  (void)cl;
   cluster_sum(part, 2 * M, [&](int t, double v) {
     const int which = t / M, c = t % M;
-    a.partN[(size_t)cl * 2 * MAXM + which * MAXM + c] = v;
+    atomicAdd(a.partN + which * MAXM + c, v);
   });
 }
 
@@ -608,14 +651,11 @@ struct Solver {
   }
 
   size_t gram_smem(int nl, int n1, int n2, bool sym2, bool csum) {
-    size_t w = (size_t)nl * M + (size_t)n1 * M + (sym2 ? 0 : (size_t)n2 * M);
-    size_t s = kTileRows * w * sizeof(T) + kTileRows * sizeof(T);
     int bl = nl * M / 4;
     int nblk = bl * (n1 * M / 4) + (sym2 ? bl * (bl + 1) / 2 : bl * (n2 * M / 4));
     int rs = std::max(1, kThreads / nblk);
     size_t len = (size_t)nblk * 16;
-    size_t r = ((rs * len * sizeof(T) + 15) / 16) * 16 + (len + (csum ? (size_t)n2 * M : 0)) * sizeof(double);
-    return std::max(s, r);
+    return (((rs * len + kThreads) * sizeof(T) + 15) / 16) * 16 + (len + (csum ? (size_t)n2 * M : 0)) * sizeof(double);
   }
 
   void launch_gram(int nl, const T* const* L, int n1, const T* const* R1, int n2, const T* const* R2,
@@ -688,7 +728,7 @@ struct Solver {
 
   void launch_rr_(int nb, int nx) {
     RRArgs r{};
-    r.sm = sm; r.smt = smt; r.is_double = sizeof(T) == 8; r.ncl = grid_gram / CL;
+    r.sm = sm; r.smt = smt; r.is_double = sizeof(T) == 8; r.ncl = 1;
     r.M = M; r.nb = nb; r.nx = nx; r.tau = tau; r.tau_p = tau_p; r.st = state;
     launch_rr(st, r, inverse_rr);
     MGE_LAUNCHED(ctx, 1);
@@ -711,14 +751,16 @@ struct Solver {
     u.Wr = Wr.p;
     u.partN = &sm->partN[0][0];
     u.st = state;
-    k_update<T, M><<<grid_upd, kThreads, 0, st>>>(u);
+    if (nb == 1) k_update<T, M, 1><<<grid_upd, kThreads, 0, st>>>(u);
+    else if (nb == 2) k_update<T, M, 2><<<grid_upd, kThreads, 0, st>>>(u);
+    else k_update<T, M, 3><<<grid_upd, kThreads, 0, st>>>(u);
     MGE_LAUNCHED(ctx, 1);
   }
 
   void launch_wprep_(bool hx, bool hp, bool check) {
     WprepArgs w{};
     w.sm = sm; w.smt = smt; w.is_double = sizeof(T) == 8;
-    w.ncl_w = grid_gram / CL; w.ncl_n = grid_upd / CL;
+    w.ncl_w = 1; w.ncl_n = 1;
     w.M = M; w.K = K; w.has_x = hx; w.has_p = hp; w.check = check;
     w.deflate = op.deflate; w.n = n; w.tol = tol; w.norm = op.norm; w.bmax = op.bmax;
     w.tau_w = tau_w; w.maxiter = maxiter; w.st = state;

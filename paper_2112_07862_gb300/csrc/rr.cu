@@ -41,6 +41,11 @@ __device__ bool load_grams(const RRArgs& a, double* gA, double* gB, int n, int l
     gB[i * ld + j] = sum_strided(&sm->partB[0][si * MAXS + sj], a.ncl, MAXS * MAXS);
   }
   __syncthreads();
+  // the accumulators start the next Gram from zero
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int i = t / n, j = t % n;
+    for (int c = 0; c < a.ncl; ++c) { a.sm->partA[c][i * MAXS + j] = 0.0; a.sm->partB[c][i * MAXS + j] = 0.0; }
+  }
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     int i = t / n, j = t % n;
     if (i < j) {
@@ -554,6 +559,545 @@ __global__ void __launch_bounds__(kRRThreads) k_rr_inv(RRArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
+// fast form for bases of at most 32 directions: the inverse-pencil algorithm above on
+// 32 x 32 shared-memory matrices, one CTA of 8 warps.  Warp w owns rows 4w .. 4w+3 of every
+// matrix update; the per-step reductions (pivot columns, Householder vectors) are
+// recomputed by every warp so that one barrier per elimination step suffices.
+//
+// Lane-dependent branches are avoided in the warp-synchronous parts: a warp left diverged
+// by such a branch executes later shuffles and barriers one thread group at a time, which
+// multiplied the cost of this kernel several times over.
+// ---------------------------------------------------------------------------------------
+constexpr int WN = 32;
+constexpr int kRWThreads = 256;
+constexpr int kRWRows = WN / (kRWThreads / 32);     // rows per warp: 4
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Four warp sums at once (transposed butterfly, six shuffles): lane l returns the total of
+// value (l >> 3) & 3.
+__device__ __forceinline__ float warp_sum4(float s0, float s1, float s2, float s3, int lane) {
+  const bool h16 = lane & 16, h8 = lane & 8;
+  float a0 = h16 ? s2 : s0, a1 = h16 ? s3 : s1;
+  const float b0 = h16 ? s0 : s2, b1 = h16 ? s1 : s3;
+  a0 += __shfl_xor_sync(0xffffffffu, b0, 16);
+  a1 += __shfl_xor_sync(0xffffffffu, b1, 16);
+  float c = h8 ? a1 : a0;
+  const float d = h8 ? a0 : a1;
+  c += __shfl_xor_sync(0xffffffffu, d, 8);
+  c += __shfl_xor_sync(0xffffffffu, c, 4);
+  c += __shfl_xor_sync(0xffffffffu, c, 2);
+  c += __shfl_xor_sync(0xffffffffu, c, 1);
+  return c;
+}
+
+__global__ void __launch_bounds__(kRWThreads) k_rr_warp(RRArgs a) {
+  if (a.st->done) return;
+  const long long clk0 = clock64();
+  __shared__ long long sclk[12];
+  // phase clocks: written by every thread (a branch around clock64 leaves warps diverged)
+#define RW_MARK(k) (sclk[k] = clock64() - clk0)
+  const int M = a.M, n = a.nb * a.M, nx = a.nx;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int row0 = wid * kRWRows;
+  __shared__ float sA[WN][WN + 1];       // G^_A and its Schur complements, then L (compact)
+  __shared__ float sB[WN][WN + 1];       // G^_B (full index), then Y = L^-1 G^_B, then T
+  __shared__ float sL[WN][WN + 1];       // L (full index), then L^-1 (compact)
+  __shared__ float sM[WN][WN + 1];       // G^_B (compact), then M = L^-1 G^_B L^-T
+  __shared__ float sH[WN][WN + 1];       // Householder vectors: sH[j][i] = v_i of reflector j
+  __shared__ float sZ[WN][MAXM + 1];     // eigenvectors (compact coordinate r, vector q)
+  __shared__ float sU[WN][MAXM + 1];
+  __shared__ float sV[WN][MAXM + 1];
+  __shared__ float sgp[MAXM][MAXM + 1];
+  __shared__ double sdsc[WN];
+  __shared__ float srd[WN], sd[WN], se[WN], se2[WN], sht[WN], sp[WN], smu[MAXM], srdp[MAXM];
+  __shared__ int sidx[WN];
+  __shared__ unsigned slive;
+  Small* sm = a.sm;
+  if (threadIdx.x < 12) sclk[threadIdx.x] = 0;
+
+  // ---- 1. FP64 Grams scaled to unit G_A diagonal, rounded to FP32 ----
+  if (wid == 0) {
+    const int li = lane < n ? lane : 0;
+    const double gaii = sm->partA[0][li * MAXS + li], gbii = sm->partB[0][li * MAXS + li];
+    const bool live = lane < n && gaii > 1e-30 && gbii > 1e-30 && gaii < 1e30 && gbii < 1e30;
+    // any positive scaling is exact enough: it is undone in C_x and C_p with the same factors
+    sdsc[lane] = live ? (double)rsqrtf((float)gaii) : 0.0;
+    const unsigned lm = __ballot_sync(0xffffffffu, live);
+    slive = lm;
+  }
+  __syncthreads();
+  int bad = 0;
+  for (int t = threadIdx.x; t < WN * WN; t += kRWThreads) {
+    const int i = t >> 5, j = t & 31;
+    const bool in = i < n && j < n;
+    const int ii = in ? i : 0, jj = in ? j : 0;
+    const double ga = 0.5 * (sm->partA[0][ii * MAXS + jj] + sm->partA[0][jj * MAXS + ii]);
+    const int bi = ii / 4, bj = jj / 4;
+    const double gb = (bi < bj) ? sm->partB[0][ii * MAXS + jj]
+                    : (bi > bj) ? sm->partB[0][jj * MAXS + ii]
+                                : 0.5 * (sm->partB[0][ii * MAXS + jj] + sm->partB[0][jj * MAXS + ii]);
+    bad |= in && !(isfinite(ga) && isfinite(gb));
+    const float sc = (float)sdsc[i] * (float)sdsc[j];
+    sA[i][j] = in ? (float)ga * sc : 0.f;
+    sB[i][j] = in ? (float)gb * sc : 0.f;
+  }
+  bad = __syncthreads_or(bad);
+  for (int t = threadIdx.x; t < n * n; t += kRWThreads) {      // the next Gram starts from zero
+    const int i = t / n, j = t % n;
+    sm->partA[0][i * MAXS + j] = 0.0;
+    sm->partB[0][i * MAXS + j] = 0.0;
+  }
+  if (bad) {
+    if (threadIdx.x == 0) { a.st->done = DONE_ERROR; a.st->err = MGE_ENOTFINITE; a.st->bad_stage = 1; }
+    return;
+  }
+  RW_MARK(1);
+
+  // ---- 2. Cholesky of G^_A with dropping: step j scales column j, every warp updates its
+  //      rows of the Schur complement (lane = column); dropped directions are skipped ----
+  unsigned keep = slive;
+  {
+    const float tau = (float)a.tau;
+#pragma unroll 1
+    for (int j = 0; j < n; ++j) {
+      const float ajj = sA[j][j];
+      const bool ok = ((keep >> j) & 1u) && ajj > tau && isfinite(ajj);
+      const float rinv = ok ? rsqrtf(ajj) : 0.f;
+      const float lj = (lane > j && lane < n) ? sA[lane][j] * rinv : 0.f;      // l_{lane j}
+      keep = ok ? keep : (keep & ~(1u << j));
+      if (wid == (j & 7)) sL[lane][j] = (lane == j) ? ajj * rinv : lj;
+      // l_kj = 0 for k <= j, so column j and the rows above j are left unchanged
+#pragma unroll
+      for (int r = 0; r < kRWRows; ++r) {
+        const float li = __shfl_sync(0xffffffffu, lj, row0 + r);
+        sA[row0 + r][lane] -= li * lj;
+      }
+      __syncthreads();
+    }
+  }
+  const int k = __popc(keep);
+  if (threadIdx.x < WN) {                    // compaction map: kept index of rank r at sidx[r]
+    const int i = threadIdx.x;
+    const bool kept = (keep >> i) & 1u;
+    const int pos = __popc(keep & ((1u << i) - 1u));
+    sidx[kept ? pos : k + (i - pos)] = kept ? i : 0;
+  }
+  RW_MARK(9);
+  if (k < M) {
+    if (threadIdx.x == 0) { a.st->done = DONE_ERROR; a.st->err = MGE_ECHOLESKY; a.st->kept = k; }
+    return;
+  }
+  if (threadIdx.x == 0 && k < n) atomicAdd(&a.st->drops, 1);
+  __syncthreads();
+  for (int t = threadIdx.x; t < WN * WN; t += kRWThreads) {
+    const int r = t >> 5, c = t & 31;
+    const bool in = r < k && c < k;
+    const int sr = sidx[r], sc = sidx[c];
+    sA[r][c] = (in && c <= r) ? sL[sr][sc] : 0.f;
+    sM[r][c] = in ? sB[sr][sc] : 0.f;
+  }
+  if (threadIdx.x < WN) {
+    const int r = threadIdx.x;
+    srd[r] = r < k ? 1.f / sL[sidx[r]][sidx[r]] : 0.f;
+  }
+  __syncthreads();
+  RW_MARK(2);
+
+  // ---- 3. L^-1 by forward substitution (row r final after step r, lane = column), then
+  //      M = L^-1 G^_B L^-T as two products ----
+  for (int t = threadIdx.x; t < WN * WN; t += kRWThreads) {
+    const int r = t >> 5, c = t & 31;
+    sL[r][c] = (r == c && r < k) ? 1.f : 0.f;
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int r = 0; r < k; ++r) {
+    const float xr = sL[r][lane] * srd[r];
+#pragma unroll
+    for (int q = 0; q < kRWRows; ++q) {
+      const int s_ = row0 + q;
+      if (s_ > r && s_ < k) sL[s_][lane] -= sA[s_][r] * xr;
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < WN * WN; t += kRWThreads) sL[t >> 5][t & 31] *= srd[t >> 5];
+  __syncthreads();
+  {
+    const int i = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 4;
+    float y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
+#pragma unroll 8
+    for (int s_ = 0; s_ < k; ++s_) {
+      const float l = sL[i][s_];
+      y0 += l * sM[s_][c0]; y1 += l * sM[s_][c0 + 1]; y2 += l * sM[s_][c0 + 2]; y3 += l * sM[s_][c0 + 3];
+    }
+    sB[i][c0] = y0; sB[i][c0 + 1] = y1; sB[i][c0 + 2] = y2; sB[i][c0 + 3] = y3;
+    __syncthreads();
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+#pragma unroll 8
+    for (int s_ = 0; s_ < k; ++s_) {
+      const float y = sB[i][s_];
+      m0 += y * sL[c0][s_]; m1 += y * sL[c0 + 1][s_]; m2 += y * sL[c0 + 2][s_]; m3 += y * sL[c0 + 3][s_];
+    }
+    sM[i][c0] = m0; sM[i][c0 + 1] = m1; sM[i][c0 + 2] = m2; sM[i][c0 + 3] = m3;
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < WN * WN; t += kRWThreads) {     // T = symmetric part of M
+    const int r = t >> 5, c = t & 31;
+    sB[r][c] = 0.5f * (sM[r][c] + sM[c][r]);
+  }
+  __syncthreads();
+  RW_MARK(3);
+
+  // ---- 4. Householder tridiagonalisation of T (in sB) ----
+#pragma unroll 1
+  for (int j = 0; j + 2 < k; ++j) {
+    const float x = (lane > j && lane < k) ? sB[lane][j] : 0.f;
+    const float s2 = warp_sum(x * x);
+    const float x0 = __shfl_sync(0xffffffffu, x, j + 1);
+    const float tail = s2 - x0 * x0;
+    const bool refl = tail > 1e-30f * s2 && s2 > 0.f;
+    const float alpha = refl ? -copysignf(sqrtf(s2), x0) : x0;
+    const float v0 = x0 - alpha;
+    const float tau = refl ? 2.f / (tail + v0 * v0) : 0.f;
+    const float v = refl ? ((lane == j + 1) ? v0 : x) : 0.f;
+    if (wid == 0) {
+      sd[j] = sB[j][j]; se[j] = alpha; sht[j] = tau;
+      sH[j][lane] = v;
+    }
+    if (refl) {
+      // p_i = tau sum_c T_ic v_c for this warp's rows (lane = c)
+      const float pr = warp_sum4(sB[row0][lane] * v, sB[row0 + 1][lane] * v, sB[row0 + 2][lane] * v,
+                                 sB[row0 + 3][lane] * v, lane);
+      const int ir = row0 + ((lane >> 3) & 3);
+      sp[ir] = (ir > j && ir < k) ? tau * pr : 0.f;
+      __syncthreads();
+      const float p = sp[lane];
+      const float K = 0.5f * tau * warp_sum(p * v);
+      const float w = p - K * v;
+#pragma unroll
+      for (int r = 0; r < kRWRows; ++r) {
+        const int i = row0 + r;
+        const float vi = __shfl_sync(0xffffffffu, v, i), wi = __shfl_sync(0xffffffffu, w, i);
+        if (i > j && i < k) sB[i][lane] -= vi * w + wi * v;
+      }
+    }
+    __syncthreads();
+  }
+  if (wid == 0) {
+    sd[k - 2] = sB[k - 2][k - 2];
+    se[k - 2] = sB[k - 1][k - 2];
+    sd[k - 1] = sB[k - 1][k - 1];
+    sht[k - 2] = 0.f;
+    __syncwarp();
+    se2[lane] = (lane + 1 < k) ? se[lane] * se[lane] : 0.f;
+  }
+  __syncthreads();
+  RW_MARK(4);
+
+  // ---- 5. the M largest eigenvalues of T: multisection bisection, one warp per eigenvalue ----
+  {
+    float glo = 3.4e38f, ghi = -3.4e38f, emax = 0.f;
+    for (int r = 0; r < k; ++r) {
+      const float rad = (r > 0 ? fabsf(se[r - 1]) : 0.f) + (r + 1 < k ? fabsf(se[r]) : 0.f);
+      glo = fminf(glo, sd[r] - rad);
+      ghi = fmaxf(ghi, sd[r] + rad);
+      emax = fmaxf(emax, fabsf(sd[r]) + rad);
+    }
+    const float pivmin = fmaxf(1e-30f, 1e-37f * emax * emax);
+    const float width = fmaxf(ghi - glo, 1e-30f);
+    glo -= 2e-6f * width + pivmin;
+    ghi += 2e-6f * width + pivmin;
+    for (int q = wid; q < M; q += kRWThreads / 32) {
+      const int target = k - 1 - q;
+      float lo = glo, hi = ghi;
+      for (int round = 0; round < 10; ++round) {
+        const float step = (hi - lo) / 33.f;
+        const float xs = lo + step * (float)(lane + 1);
+        const int cnt = sturm_count(sd, se2, k, xs, pivmin);
+        const unsigned above = __ballot_sync(0xffffffffu, cnt > target);
+        float nlo = lo, nhi = hi;
+        if (above) {
+          const int f = __ffs(above) - 1;
+          nhi = __shfl_sync(0xffffffffu, xs, f);
+          const float pl = __shfl_sync(0xffffffffu, xs, f > 0 ? f - 1 : 0);
+          nlo = f > 0 ? pl : lo;
+        } else {
+          nlo = __shfl_sync(0xffffffffu, xs, 31);
+        }
+        lo = nlo; hi = nhi;
+        if (hi - lo <= 1.2e-7f * fmaxf(fabsf(lo), fabsf(hi))) break;
+      }
+      smu[q] = 0.5f * (lo + hi);
+    }
+  }
+  __syncthreads();
+  RW_MARK(5);
+
+  // ---- 6. inverse iteration on T - mu I (tridiagonal LU with partial pivoting), one thread
+  //      per eigenvalue; loops unrolled over the 32 possible rows so that the factors stay in
+  //      registers, pivoting by selects (no divergence between the eigenvalues) ----
+  for (int q = threadIdx.x; q < M; q += kRWThreads) {
+    float nrmT = 0.f;
+    for (int r = 0; r < k; ++r)
+      nrmT = fmaxf(nrmT, fabsf(sd[r]) + (r > 0 ? fabsf(se[r - 1]) : 0.f) + (r + 1 < k ? fabsf(se[r]) : 0.f));
+    const float tiny = fmaxf(nrmT * 1.2e-7f, 1e-30f);
+    const float lam = smu[q];
+    float u0[WN], u1[WN], lm[WN], y[WN];     // reciprocal pivots, first superdiagonal, multipliers
+    unsigned pvm = 0u;                       // bit r: rows r and r + 1 exchanged
+    float p = sd[0] - lam, qq = se[0];
+#pragma unroll
+    for (int r = 0; r < WN; ++r) {
+      if (r + 1 < k) {
+        const float c = se[r], an = sd[r + 1] - lam, bn = (r + 2 < k) ? se[r + 1] : 0.f;
+        const bool piv = fabsf(c) > fabsf(p);
+        const float pc = (fabsf(p) < tiny) ? copysignf(tiny, p == 0.f ? 1.f : p) : p;
+        const float id = __fdividef(1.f, piv ? c : pc);
+        const float l = (piv ? p : c) * id;
+        u0[r] = id;
+        u1[r] = piv ? an : qq;
+        lm[r] = l;
+        pvm |= piv ? (1u << r) : 0u;
+        const float np = piv ? qq - l * an : an - l * qq;
+        qq = piv ? -l * bn : bn;
+        p = np;
+      } else if (r + 1 == k) {
+        const float pc = (fabsf(p) < tiny) ? copysignf(tiny, p == 0.f ? 1.f : p) : p;
+        u0[r] = __fdividef(1.f, pc);
+        u1[r] = 0.f;
+        lm[r] = 0.f;
+      } else {
+        u0[r] = 0.f; u1[r] = 0.f; lm[r] = 0.f;
+      }
+      y[r] = (r < k) ? 1.f + 0.37f * __sinf(1.3f * r + 0.7f * q) : 0.f;
+    }
+#pragma unroll 1
+    for (int itn = 0; itn < 2; ++itn) {
+#pragma unroll
+      for (int r = 0; r + 1 < WN; ++r) {
+        if (r + 1 < k) {
+          const bool piv = (pvm >> r) & 1u;
+          const float a0 = piv ? y[r + 1] : y[r], a1 = piv ? y[r] : y[r + 1];
+          y[r] = a0;
+          y[r + 1] = a1 - lm[r] * a0;
+        }
+      }
+      float mx = 0.f;
+#pragma unroll
+      for (int r = WN - 1; r >= 0; --r) {
+        if (r < k) {
+          float v = y[r];
+          if (r + 1 < WN && r + 1 < k) v -= u1[r] * y[r + 1];
+          // the second superdiagonal is nonzero only where rows were exchanged
+          if (r + 2 < WN && r + 2 < k && ((pvm >> r) & 1u)) v -= se[r + 1] * y[r + 2];
+          v *= u0[r];
+          y[r] = v;
+          mx = fmaxf(mx, fabsf(v));
+        }
+      }
+      const float inv = (mx > 0.f && isfinite(mx)) ? 1.f / mx : 1.f;
+#pragma unroll
+      for (int r = 0; r < WN; ++r) y[r] *= inv;
+    }
+#pragma unroll
+    for (int r = 0; r < WN; ++r) sZ[r][q] = y[r];
+  }
+  __syncthreads();
+  RW_MARK(6);
+
+  // ---- 7. CGS2 (warp 0, lane = coordinate), then the back-transform y <- H_0 ... H_{k-3} y
+  //      (vector q by warp q mod 8) ----
+  if (wid == 0) {
+#pragma unroll 1
+    for (int j = 0; j < M; ++j) {
+      float zj = sZ[lane][j];
+#pragma unroll 1
+      for (int pass = 0; pass < 2; ++pass) {
+        int i2 = 0;
+#pragma unroll 1
+        for (; i2 + 4 <= j; i2 += 4) {
+          const float z0 = sZ[lane][i2], z1 = sZ[lane][i2 + 1], z2 = sZ[lane][i2 + 2], z3 = sZ[lane][i2 + 3];
+          float d0 = z0 * zj, d1 = z1 * zj, d2 = z2 * zj, d3 = z3 * zj;
+#pragma unroll
+          for (int o = 16; o; o >>= 1) {
+            d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+            d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+            d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+            d3 += __shfl_xor_sync(0xffffffffu, d3, o);
+          }
+          zj -= d0 * z0 + d1 * z1 + d2 * z2 + d3 * z3;
+        }
+#pragma unroll 1
+        for (; i2 < j; ++i2) {
+          const float zi = sZ[lane][i2];
+          zj -= warp_sum(zi * zj) * zi;
+        }
+      }
+      const float nn = warp_sum(zj * zj);
+      sZ[lane][j] = (nn > 0.f) ? zj * rsqrtf(nn) : 0.f;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int q = wid; q < M; q += kRWThreads / 32) {
+    float z = sZ[lane][q];
+#pragma unroll 1
+    for (int j = k - 3; j >= 0; --j) {
+      const float tj = sht[j], hv = sH[j][lane];
+      z -= tj * warp_sum(hv * z) * hv;
+    }
+    sZ[lane][q] = (lane < k) ? z : 0.f;
+  }
+  __syncthreads();
+  RW_MARK(7);
+
+  // ---- 8. Ritz coefficients: z = L^-T y, C_x = D z / sqrt(mu), Lambda = 1 / mu ----
+  for (int t = threadIdx.x; t < WN * M; t += kRWThreads) {
+    const int r = t / M, q = t % M;
+    float v = 0.f;
+#pragma unroll 8
+    for (int s_ = 0; s_ < k; ++s_) v += sL[s_][r] * sZ[s_][q];
+    sU[r][q] = v;
+  }
+  for (int t = threadIdx.x; t < MAXS * MAXM; t += kRWThreads) { sm->Cx[t] = 0.0; sm->Cp[t] = 0.0; }
+  const int badmu = __syncthreads_or(threadIdx.x < M && !(smu[threadIdx.x] > 0.f && isfinite(smu[threadIdx.x])));
+  if (badmu) {
+    if (threadIdx.x == 0) { a.st->done = DONE_ERROR; a.st->err = MGE_ENOTFINITE; a.st->bad_stage = 4; }
+    return;
+  }
+  for (int t = threadIdx.x; t < k * M; t += kRWThreads) {
+    const int r = t / M, q = t % M;
+    sm->Cx[sidx[r] * MAXM + q] = sdsc[sidx[r]] * (double)(sU[r][q] * rsqrtf(smu[q]));
+  }
+  if (threadIdx.x < M) sm->lam[threadIdx.x] = 1.0 / (double)smu[threadIdx.x];
+  RW_MARK(8);
+
+  // ---- 9. C_p: in u = L^T z coordinates the G_B inner product is u^T M u'; the Ritz vectors
+  //      are y / sqrt(mu) with M y = mu y, so M-orthogonality to them is orthogonality to y.
+  //      All matrices are zero outside k x k, so the sums run over all 32 indices. ----
+  if (nx > 0) {
+    if (threadIdx.x < WN) sp[threadIdx.x] = (threadIdx.x < k && sidx[threadIdx.x] >= nx) ? 1.f : 0.f;
+    __syncthreads();
+    for (int t = threadIdx.x; t < WN * M; t += kRWThreads) {    // u = L^T z_p (X rows of z zeroed)
+      const int r = t / M, q = t % M;
+      float v0 = 0.f, v1 = 0.f;
+#pragma unroll
+      for (int s_ = 0; s_ < WN; s_ += 2) {
+        v0 += sA[s_][r] * (sU[s_][q] * sp[s_]);
+        v1 += sA[s_ + 1][r] * (sU[s_ + 1][q] * sp[s_ + 1]);
+      }
+      sV[r][q] = v0 + v1;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < M * M; t += kRWThreads) {     // Y^T u
+      const int i2 = t / M, q = t % M;
+      float v0 = 0.f, v1 = 0.f;
+#pragma unroll
+      for (int r = 0; r < WN; r += 2) {
+        v0 += sZ[r][i2] * sV[r][q];
+        v1 += sZ[r + 1][i2] * sV[r + 1][q];
+      }
+      sgp[i2][q] = v0 + v1;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < WN * M; t += kRWThreads) {    // u <- u - Y (Y^T u)
+      const int r = t / M, q = t % M;
+      float v = sV[r][q];
+#pragma unroll
+      for (int i2 = 0; i2 < MAXM; ++i2)
+        if (i2 < M) v -= sZ[r][i2] * sgp[i2][q];
+      sU[r][q] = v;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < WN * M; t += kRWThreads) {    // M u
+      const int r = t / M, q = t % M;
+      float v0 = 0.f, v1 = 0.f;
+#pragma unroll
+      for (int c = 0; c < WN; c += 2) {
+        v0 += sM[r][c] * sU[c][q];
+        v1 += sM[r][c + 1] * sU[c + 1][q];
+      }
+      sV[r][q] = v0 + v1;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < MAXM * MAXM; t += kRWThreads) {   // G_p = u^T M u (zero padded)
+      const int i2 = t / MAXM, q = t % MAXM;
+      float v0 = 0.f, v1 = 0.f;
+      if (i2 < M && q < M) {
+#pragma unroll
+        for (int r = 0; r < WN; r += 2) {
+          v0 += sU[r][i2] * sV[r][q];
+          v1 += sU[r + 1][i2] * sV[r + 1][q];
+        }
+      }
+      sgp[i2][q] = v0 + v1;
+    }
+    __syncthreads();
+    if (wid == 0) {                 // Cholesky of G_p with dropping (lower triangle), lane = row
+      const float tp = (float)a.tau_p;
+#pragma unroll 1
+      for (int j = 0; j < M; ++j) {
+        const float gjj = sgp[j][j];
+        const bool ok = gjj > tp && isfinite(gjj);
+        const float rinv = ok ? rsqrtf(gjj) : 0.f;
+        const int rl = lane < MAXM ? lane : 0;
+        const float lj = (lane > j && lane < M) ? sgp[rl][j] * rinv : 0.f;
+        __syncwarp();
+        const float dj = (lane == j) ? gjj * rinv : lj;
+        if (lane < MAXM) sgp[lane][j] = dj;
+        // l_cj = 0 for c <= j: entries above the diagonal pick up values that are never read
+#pragma unroll
+        for (int c = 0; c < MAXM; ++c) {
+          const float lc = __shfl_sync(0xffffffffu, lj, c);
+          if (c > j && lane < MAXM) sgp[lane][c] -= lj * lc;
+        }
+        __syncwarp();
+      }
+      if (lane < M) srdp[lane] = sgp[lane][lane] > 0.f ? 1.f / sgp[lane][lane] : 0.f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < k; r += kRWThreads) {         // u <- u L_p^-T, row by row
+      float ur[MAXM];
+#pragma unroll
+      for (int c = 0; c < MAXM; ++c) {
+        if (c < M) {
+          float v = sU[r][c];
+#pragma unroll
+          for (int s_ = 0; s_ < c; ++s_) v -= ur[s_] * sgp[c][s_];
+          ur[c] = v * srdp[c];
+          sU[r][c] = ur[c];
+        } else {
+          ur[c] = 0.f;
+        }
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < k * M; t += kRWThreads) {     // z_p = L^-T u, C_p = D z_p
+      const int r = t / M, q = t % M;
+      float v0 = 0.f, v1 = 0.f;
+#pragma unroll
+      for (int s_ = 0; s_ < WN; s_ += 2) {
+        v0 += sL[s_][r] * sU[s_][q];
+        v1 += sL[s_ + 1][r] * sU[s_ + 1][q];
+      }
+      sm->Cp[sidx[r] * MAXM + q] = sdsc[sidx[r]] * (double)(v0 + v1);
+    }
+  }
+  __syncthreads();
+  if (a.is_double) store_coeffs<double, float>(a);
+  else store_coeffs<float, float>(a);
+  RW_MARK(11);
+  __syncthreads();
+  if (threadIdx.x < 12) a.st->rr_clk[threadIdx.x] = sclk[threadIdx.x];
+  if (threadIdx.x == 0) a.st->kept = k;
+#undef RW_MARK
+}
+
+// ---------------------------------------------------------------------------------------
 // FP64 form: Cholesky of G^_B with dropping, standard form, cyclic two-sided Jacobi
 // ---------------------------------------------------------------------------------------
 __device__ int jacobi_eig(double* A, double* V, int ld, int k) {
@@ -855,6 +1399,15 @@ __global__ void __launch_bounds__(kThreads) k_wprep(WprepArgs a) {
   }
   const int ox = 0, op = a.has_x ? M : 0, ow = (a.has_x ? M : 0) + (a.has_p ? M : 0);
   const double inv_n = 1.0 / (double)a.n;
+  // the accumulators start the next reduction from zero (everything was read above)
+  for (int t = threadIdx.x; t < rows * M; t += blockDim.x) {
+    int i = t / M, j = t % M;
+    for (int c = 0; c < a.ncl_w; ++c) sm->partW[c][i * MAXM + j] = 0.0;
+  }
+  for (int t = threadIdx.x; t < MAXM; t += blockDim.x) {
+    for (int c = 0; c < a.ncl_w; ++c) sm->partC[c][t] = 0.0;
+    for (int c = 0; c < a.ncl_n; ++c) { sm->partN[c][t] = 0.0; sm->partN[c][MAXM + t] = 0.0; }
+  }
   for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
     int i = t / M, j = t % M;
     // R-precision subtraction: entries below tau_w * G_jj are dropped anyway
@@ -930,7 +1483,8 @@ cudaError_t rr_configure() {
 
 void launch_rr(cudaStream_t st, const RRArgs& a, bool inverse_form) {
   int n = a.nb * a.M;
-  if (inverse_form) k_rr_inv<<<1, kRRThreads, rr_inv_smem(n), st>>>(a);
+  if (inverse_form && n <= WN) k_rr_warp<<<1, kRWThreads, 0, st>>>(a);
+  else if (inverse_form) k_rr_inv<<<1, kRRThreads, rr_inv_smem(n), st>>>(a);
   else k_rr_jacobi<<<1, kThreads, rr_jacobi_smem(n), st>>>(a);
 }
 
