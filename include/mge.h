@@ -161,6 +161,26 @@ mge_status mge_ops_export(const mge_ops* ops, int64_t* a_ptr, int32_t* a_col, do
 mge_status mge_ops_apply(mge_ctx* ctx, const mge_ops* ops, int which, int precision, int m,
                          const void* X, void* Y, void* stream);
 
+/* Y = A Y (which = 0) or Y = Q Y (which = 1) in place, for callers that cannot allocate
+ * device memory: a process that reserves its whole device-memory budget up front (a
+ * serving process, or one sharing the GPU under a fixed quota), or code that must not
+ * call cudaMalloc/cudaFree because cudaFree waits for the whole device and would stall
+ * the work on its other streams.  The paper has no counterpart; it is a service entry
+ * point around the SpMM of the iteration (same kernel, same results as mge_ops_apply).
+ *
+ * XY: device pointer, row-major [n x m] block of the given precision (MGE_FP64 or
+ * MGE_FP32), 16-byte aligned, m in {4, 8, 12, 16, 24}; overwritten with the product.
+ * The copy of the block the product needs goes into one fixed 32 MiB device array inside
+ * the library (not counted in the context's HBM budget); a block whose size
+ * n * m * sizeof(element) exceeds 32 MiB is rejected with MGE_EINVAL.  Nothing in the array
+ * needs to start at zero.  Every call on a device shares the array: calls must not
+ * overlap in time (from several host threads, or on streams the caller does not order).
+ * The call returns after the product is complete (the stream is synchronised).  The first
+ * call on each device performs a set-up step (it looks up the array's device address);
+ * make that first call before any stream capture begins.  Allocates no memory. */
+mge_status mge_ops_apply_inplace(mge_ctx* ctx, const mge_ops* ops, int which, int precision, int m,
+                                 void* XY, void* stream);
+
 /* ---- embedding: LOBPCG for the first K generalized eigenpairs (Sec. 4.3) ------------- */
 
 typedef struct {

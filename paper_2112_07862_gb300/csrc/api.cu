@@ -246,6 +246,24 @@ mge_status mge_ops_apply(mge_ctx* c, const mge_ops* o, int which, int precision,
   return MGE_OK;
 }
 
+mge_status mge_ops_apply_inplace(mge_ctx* c, const mge_ops* o, int which, int precision, int m, void* XY,
+                                 void* stream) {
+  if (!c || !o || !XY || (which != 0 && which != 1)) return MGE_EINVAL;
+  if (c->impl.closed) return MGE_EINVAL;
+  Ctx* ctx = &c->impl;
+  cudaSetDevice(ctx->device);
+  if (precision != MGE_FP64 && precision != MGE_FP32) {
+    set_error(ctx, "apply_inplace: precision %d not supported", precision);
+    return MGE_EINVAL;
+  }
+  if (round_block_width(m) != m) { set_error(ctx, "apply_inplace: unsupported width %d", m); return MGE_EINVAL; }
+  cudaStream_t st = pick_stream(ctx, stream);
+  LobOp l = make_op(o->impl, which, precision);
+  MGE_TRY(spmm_apply_inplace(ctx, st, l, precision, m, XY));
+  MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  return MGE_OK;
+}
+
 mge_status mge_embed(mge_ctx* c, const mge_ops* o, int K, double tol, const mge_embed_opts* opts,
                      double* lambda, void* V, mge_embed_info* info) {
   if (!c || !o || !lambda) return MGE_EINVAL;

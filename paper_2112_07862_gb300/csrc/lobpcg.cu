@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 namespace mge {
 namespace lob {
@@ -1012,6 +1013,56 @@ mge_status spmm_apply(Ctx* ctx, cudaStream_t st, const LobOp& op, int precision,
   }
   set_error(ctx, "unsupported precision %d / width %d for apply", precision, m);
   return MGE_EINVAL;
+}
+
+// ---------------------------------------------------------------------------------------
+// In-place apply that allocates nothing.  The SpMM reads the rows of X at a row's
+// neighbours while it writes that row of Y, so Y = A Y needs a copy of the block; the copy
+// goes into one fixed device array that every call on the device shares.  Nothing in the
+// array has to start at zero: each call overwrites the bytes it reads before reading them.
+// Two calls whose copies or kernels overlap in time (several host threads, or streams the
+// caller does not order) race on the array.
+// ---------------------------------------------------------------------------------------
+constexpr size_t kInplaceScratchBytes = size_t(32) << 20;      // 32 MiB per device
+static __device__ __align__(256) unsigned char g_inplace_scratch[kInplaceScratchBytes];
+
+namespace {
+constexpr int kInplaceMaxDevices = 64;
+std::mutex g_inplace_mu;
+void* g_inplace_addr[kInplaceMaxDevices] = {};
+}  // namespace
+
+size_t inplace_scratch_bytes() { return kInplaceScratchBytes; }
+
+mge_status spmm_apply_inplace(Ctx* ctx, cudaStream_t st, const LobOp& op, int precision, int m, void* XY) {
+  const size_t elem = precision == MGE_FP64 ? sizeof(double) : sizeof(float);
+  const size_t bytes = (size_t)op.n * (size_t)m * elem;
+  if (bytes > kInplaceScratchBytes) {
+    set_error(ctx, "apply_inplace: the block (%lld x %d, %zu bytes) exceeds the fixed %zu-byte scratch",
+              (long long)op.n, m, bytes, kInplaceScratchBytes);
+    return MGE_EINVAL;
+  }
+  if (ctx->device < 0 || ctx->device >= kInplaceMaxDevices) {
+    set_error(ctx, "apply_inplace: device ordinal %d out of range", ctx->device);
+    return MGE_EINVAL;
+  }
+  void* scratch = nullptr;
+  {
+    // set-up, once per device, with that device current (the caller made it current)
+    std::lock_guard<std::mutex> lock(g_inplace_mu);
+    if (!g_inplace_addr[ctx->device]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_inplace_scratch);
+      if (e != cudaSuccess || !p) {
+        set_error(ctx, "apply_inplace: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        return MGE_EDEVICE;
+      }
+      g_inplace_addr[ctx->device] = p;
+    }
+    scratch = g_inplace_addr[ctx->device];
+  }
+  MGE_CUDA(ctx, cudaMemcpyAsync(scratch, XY, bytes, cudaMemcpyDeviceToDevice, st));
+  return spmm_apply(ctx, st, op, precision, m, scratch, XY);
 }
 
 }  // namespace mge

@@ -146,6 +146,9 @@ mge_status lobpcg_solve(Ctx* ctx, cudaStream_t st, const LobOp& op, int precisio
 
 mge_status spmm_apply(Ctx* ctx, cudaStream_t st, const LobOp& op, int precision, int m,
                       const void* X, void* Y);
+// Y = A Y through a fixed device array (no allocation); see lobpcg.cu.
+mge_status spmm_apply_inplace(Ctx* ctx, cudaStream_t st, const LobOp& op, int precision, int m, void* XY);
+size_t inplace_scratch_bytes();
 
 // supported block widths
 inline int round_block_width(int m) {

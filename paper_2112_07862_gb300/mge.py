@@ -25,7 +25,7 @@ PRECISION = {"fp64": MGE_FP64, "fp32": MGE_FP32, "bf16": MGE_BF16}
 EXPORTS = [
     "mge_create", "mge_destroy", "mge_strerror", "mge_ctx_last_error", "mge_ctx_stats",
     "mge_ctx_set_timing", "mge_ctx_reset_stats", "mge_build_graph_ops", "mge_ops_destroy",
-    "mge_ops_info", "mge_ops_export", "mge_ops_apply", "mge_embed", "mge_submit", "mge_poll",
+    "mge_ops_info", "mge_ops_export", "mge_ops_apply", "mge_ops_apply_inplace", "mge_embed", "mge_submit", "mge_poll",
     "mge_release",
 ]
 
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH):
         "mge_ops_info": (i, [vp, C.POINTER(mge_ops_info_t)]),
         "mge_ops_export": (i, [vp, vp, vp, vp, vp, vp, vp, vp, vp, i]),
         "mge_ops_apply": (i, [vp, vp, i, i, i, vp, vp, vp]),
+        "mge_ops_apply_inplace": (i, [vp, vp, i, i, i, vp, vp]),
         "mge_embed": (i, [vp, vp, i, d, C.POINTER(mge_embed_opts), vp, vp, C.POINTER(mge_embed_info)]),
         "mge_submit": (i, [vp, C.POINTER(mge_request), C.POINTER(u64)]),
         "mge_poll": (i, [vp, u64, i, C.POINTER(mge_result)]),
@@ -209,6 +210,13 @@ def mge_ops_apply(ctx, ops, which: int, precision: int, m: int, X, Y, stream=Non
     """Y = A X (which=0) or Q X (which=1); X, Y torch CUDA tensors [n, m] row-major."""
     s = load().mge_ops_apply(ctx, ops, which, precision, m, _ptr(X), _ptr(Y), stream)
     return _check(ctx, s, "mge_ops_apply")
+
+
+def mge_ops_apply_inplace(ctx, ops, which: int, precision: int, m: int, XY, stream=None) -> int:
+    """XY <- A XY (which=0) or Q XY (which=1) in place; XY a torch CUDA tensor [n, m].  The
+    library allocates nothing for it (a fixed 32 MiB device array holds the copy)."""
+    s = load().mge_ops_apply_inplace(ctx, ops, which, precision, m, _ptr(XY), stream)
+    return _check(ctx, s, "mge_ops_apply_inplace")
 
 
 def mge_embed(ctx, ops, K: int, tol: float, opts: mge_embed_opts | None = None, V=None):
