@@ -707,8 +707,12 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
   MGE_TRY(ops->a_col.alloc(ctx, ops->nnz_a));
   MGE_TRY(ops->a_val.alloc(ctx, ops->nnz_a));
   MGE_TRY(ops->a_val32.alloc(ctx, ops->nnz_a));
-  MGE_TRY(ops->b.alloc(ctx, n));
-  MGE_TRY(ops->b32.alloc(ctx, n));
+  // b carries 4 zeroed elements past n: the LOBPCG Gram copies b in tiles whose byte
+  // count is rounded up to a multiple of 16
+  MGE_TRY(ops->b.alloc(ctx, n + 4));
+  MGE_TRY(ops->b32.alloc(ctx, n + 4));
+  MGE_CUDA(ctx, cudaMemsetAsync(ops->b.p + n, 0, 4 * sizeof(double), st));
+  MGE_CUDA(ctx, cudaMemsetAsync(ops->b32.p + n, 0, 4 * sizeof(float), st));
   MGE_TRY(ops->dinv_a.alloc(ctx, n));
   MGE_TRY(ops->dinv_a32.alloc(ctx, n));
   DevBuf<double> r, logr;

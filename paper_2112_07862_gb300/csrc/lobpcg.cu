@@ -43,7 +43,7 @@ struct SpmmArgs {
   T shift;
   const T* Wr;
   const T* X; const T* AX; const T* P; const T* AP;   // NULL when absent
-  const SmallT<T>* sm;                                 // Mx, Mp, Linv, cmean (NULL: plain A*Wr)
+  const SmallT<T>* sm;                                 // L, M_x L, M_p L, c L (NULL: plain A*Wr)
   T* W; T* AW;
   const State* st;
 };
@@ -65,17 +65,17 @@ __global__ void __launch_bounds__(kThreads) k_spmm_w(SpmmArgs<T> a) {
   using Sh = SpmmShape<M>;
   constexpr int G = Sh::G, S = Sh::S, TEAM = Sh::TEAM, RPW = Sh::RPW;
   constexpr int NW = kThreads / 32;
-  __shared__ T sMx[M * M], sMp[M * M], sL[M * M], sc[M];
+  __shared__ T sMxL[M * M], sMpL[M * M], sL[M * M], scL[M];
   __shared__ T sW[NW][RPW][M], sAW[NW][RPW][M];
   const bool fused = a.sm != nullptr;
   if (fused) {
     for (int t = threadIdx.x; t < M * M; t += kThreads) {
       int r = t / M, c = t % M;
-      sMx[t] = a.sm->Mx[r * MAXM + c];
-      sMp[t] = a.sm->Mp[r * MAXM + c];
+      sMxL[t] = a.sm->MxL[r * MAXM + c];
+      sMpL[t] = a.sm->MpL[r * MAXM + c];
       sL[t] = a.sm->Linv[r * MAXM + c];
     }
-    for (int t = threadIdx.x; t < M; t += kThreads) sc[t] = a.sm->cmean[t];
+    for (int t = threadIdx.x; t < M; t += kThreads) scL[t] = a.sm->cL[t];
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -128,66 +128,50 @@ __global__ void __launch_bounds__(kThreads) k_spmm_w(SpmmArgs<T> a) {
       }
       continue;
     }
+    // projection against X, P and the constant vector, then the normalisation, folded into
+    // one product per output (L, M_x L, M_p L, c L prepared by the small kernel):
+    //   W  = W_raw L - X (M_x L) - P (M_p L) - 1 (c L)
+    //   AW = (A W_raw) L - shift 1 (c L) - AX (M_x L) - AP (M_p L)
+    // the row's W_raw and A W_raw go to shared memory; lane tl of the team then computes
+    // outputs tl, tl + TEAM, ... (W column o for o < M, AW column o - M otherwise)
     if (lead) {
-      T wt[4], awt[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        wt[q] = wi[q] - sc[c0 + q];
-        awt[q] = a.shift * wt[q] + acc[q];
-      }
-      if (a.X) {
-#pragma unroll
-        for (int l = 0; l < M; l += 4) {
-          T xl[4], axl[4];
-          ldg4(a.X + row * M + l, xl);
-          ldg4(a.AX + row * M + l, axl);
-#pragma unroll
-          for (int t = 0; t < 4; ++t)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              T m = sMx[(l + t) * M + c0 + q];
-              wt[q] -= xl[t] * m;
-              awt[q] -= axl[t] * m;
-            }
-        }
-      }
-      if (a.P) {
-#pragma unroll
-        for (int l = 0; l < M; l += 4) {
-          T pl[4], apl[4];
-          ldg4(a.P + row * M + l, pl);
-          ldg4(a.AP + row * M + l, apl);
-#pragma unroll
-          for (int t = 0; t < 4; ++t)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              T m = sMp[(l + t) * M + c0 + q];
-              wt[q] -= pl[t] * m;
-              awt[q] -= apl[t] * m;
-            }
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        sW[wid][team][c0 + q] = wt[q];
-        sAW[wid][team][c0 + q] = awt[q];
+        sW[wid][team][c0 + q] = wi[q];
+        sAW[wid][team][c0 + q] = a.shift * wi[q] + acc[q];
       }
     }
     __syncwarp();
-    if (lead) {
-      T o[4] = {0, 0, 0, 0}, ao[4] = {0, 0, 0, 0};
+    if (valid) {
+      for (int o = tl; o < 2 * M; o += TEAM) {
+        const bool isw = o < M;
+        const int c = isw ? o : o - M;
+        const T* v = isw ? sW[wid][team] : sAW[wid][team];
+        T r = (isw ? T(-1) : -a.shift) * scL[c];
 #pragma unroll
-      for (int l = 0; l < M; ++l) {
-        T w = sW[wid][team][l], aw = sAW[wid][team][l];
+        for (int l = 0; l < M; ++l) r += v[l] * sL[l * M + c];
+        if (a.X) {
+          const T* xr = (isw ? a.X : a.AX) + row * M;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          T li = sL[l * M + c0 + q];
-          o[q] += w * li;
-          ao[q] += aw * li;
+          for (int l = 0; l < M; l += 4) {
+            T xv[4];
+            ldg4(xr + l, xv);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) r -= xv[t] * sMxL[(l + t) * M + c];
+          }
         }
+        if (a.P) {
+          const T* pr = (isw ? a.P : a.AP) + row * M;
+#pragma unroll
+          for (int l = 0; l < M; l += 4) {
+            T pv[4];
+            ldg4(pr + l, pv);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) r -= pv[t] * sMpL[(l + t) * M + c];
+          }
+        }
+        (isw ? a.W : a.AW)[row * M + c] = r;
       }
-      st4(a.W + row * M + c0, o);
-      st4(a.AW + row * M + c0, ao);
     }
     __syncwarp();
   }
@@ -195,26 +179,32 @@ __global__ void __launch_bounds__(kThreads) k_spmm_w(SpmmArgs<T> a) {
 
 // =======================================================================================
 // Gram products over row tiles: out1 = L^T R1, out2 = L^T diag(b) R2 (block-upper part of
-// L^T B L when R2 is L).  4x4 output blocks per thread; per-tile sums are added into
-// compensated (Neumaier) per-thread accumulators.
+// L^T B L when R2 is L).  Each CTA streams its contiguous rows through a ring of shared-
+// memory stages filled by 1-D bulk copies (TMA), one per source block and tile; threads own
+// 4x4 output blocks and accumulate them from shared memory, with a compensated fold of the
+// per-chunk sums.
 // =======================================================================================
 template <typename T>
 struct GramArgs {
   int64_t n;
   int nl, n1, n2;
-  const T* L[3];
-  const T* R1[3];
-  const T* R2[3];
   bool sym2;
-  const T* b;                // NULL = unit weights
-  double* out1;              // per-cluster partial of out1, [ncl][MAXS * MAXS], ld MAXS
-  double* out2;              // per-cluster partial of out2, leading dimension ld2
+  const T* b;                // NULL = unit weights; else at least n rounded up to 4 elements
+  double* out1;              // accumulator of out1, [MAXS * MAXS], ld MAXS
+  double* out2;              // accumulator of out2, leading dimension ld2
   int ld2;
-  int stride2;               // elements between clusters in out2
-  double* csum;              // per-cluster column sums of R2, [ncl][MAXM] (NULL: skip)
-  const State* st;
+  int stride2;
+  double* csum;              // column sums of R2 (deflation), [MAXM] (NULL: skip)
+  State* st;
+  const T* src[9];           // distinct source blocks, each [n x M] row-major
+  int nsrc;
+  int lmap[3], r1map[3], r2map[3];   // source index of each block of L, R1, R2
+  int tr;                    // rows per tile, a multiple of 4
+  int64_t per;               // rows per CTA, a multiple of tr
+  uint32_t stage_bytes;      // bytes per stage, a multiple of 128
 };
 
+constexpr int kGramStages = 4;
 constexpr int kTileRows = 32;
 
 // Neumaier's compensated step acc += x, the lost low part collected in cmp; all in the
@@ -248,7 +238,9 @@ template <typename T, int M>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads) k_gram(GramArgs<T> a) {
   if (a.st && a.st->done) return;
   using A = T;   // accumulate in the block precision (FP32 for FP32 blocks), compensated
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);       // one mbarrier per stage
+  unsigned char* data = smem_raw + 128;
   const int wl = a.nl * M, w1 = a.n1 * M, ws = a.sym2 ? 0 : a.n2 * M;
   const int bl = wl / 4, b1 = w1 / 4, b2 = (a.sym2 ? wl : a.n2 * M) / 4;
   const int nb1 = bl * b1;
@@ -261,126 +253,154 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads) k_gram(Gr
   const int rg = threadIdx.x / tpi;
   const int ti = threadIdx.x % tpi;
   const bool has_group = rg < rs;
-  // each item: a 4x4 block of one product; its two 4-wide column slices as row pointers
-  const T* lp[IPT];
-  const T* rp[IPT];
-  int it_prod[IPT], it_i[IPT], it_j[IPT];
+  const int tr = a.tr;
+  // each item: a 4x4 block of one product; offsets of its two 4-column slices in a stage
+  int lo[IPT], ro[IPT];
   bool it_ok[IPT], it_w[IPT];
 #pragma unroll
   for (int u = 0; u < IPT; ++u) {
-    int item = ti + u * tpi;
+    const int item = ti + u * tpi;
     it_ok[u] = has_group && item < nblk;
-    it_prod[u] = 0; it_i[u] = 0; it_j[u] = 0; it_w[u] = false;
-    lp[u] = rp[u] = nullptr;
+    lo[u] = ro[u] = 0;
+    it_w[u] = false;
     if (it_ok[u]) {
-      decode_item(item, nb1, b1, bl, a.sym2, b2, it_prod[u], it_i[u], it_j[u]);
-      const int ci = it_i[u] * 4, cj = it_j[u] * 4;
-      lp[u] = a.L[ci / M] + ci % M;
-      if (it_prod[u] == 1) rp[u] = a.R1[cj / M] + cj % M;
-      else if (a.sym2) { rp[u] = a.L[cj / M] + cj % M; it_w[u] = true; }
-      else { rp[u] = a.R2[cj / M] + cj % M; it_w[u] = true; }
+      int prod, bi, bj;
+      decode_item(item, nb1, b1, bl, a.sym2, b2, prod, bi, bj);
+      const int ci = bi * 4, cj = bj * 4;
+      lo[u] = a.lmap[ci / M] * tr * M + ci % M;
+      if (prod == 1) ro[u] = a.r1map[cj / M] * tr * M + cj % M;
+      else if (a.sym2) { ro[u] = a.lmap[cj / M] * tr * M + cj % M; it_w[u] = true; }
+      else { ro[u] = a.r2map[cj / M] * tr * M + cj % M; it_w[u] = true; }
     }
   }
-  // this CTA's contiguous rows
-  const int64_t per = (a.n + gridDim.x - 1) / gridDim.x;
-  const int64_t r0 = (int64_t)blockIdx.x * per;
-  const int64_t r1 = min(a.n, r0 + per);
-  A acc[IPT][16], cmp[IPT][16];
-#pragma unroll
-  for (int u = 0; u < IPT; ++u)
-#pragma unroll
-    for (int e = 0; e < 16; ++e) { acc[u][e] = A(0); cmp[u][e] = A(0); }
-  constexpr int U = 4;                  // rows in flight per thread
-  constexpr int CHUNK = 16;             // row steps summed before the compensated fold
-  int steps = 0;
-  A at[IPT][16];
-#pragma unroll
-  for (int u = 0; u < IPT; ++u)
-#pragma unroll
-    for (int e = 0; e < 16; ++e) at[u][e] = A(0);
-  for (int64_t r = r0 + rg; r < r1; r += (int64_t)rs * U) {
-#pragma unroll
-    for (int u = 0; u < IPT; ++u) {
-      if (!it_ok[u]) continue;
-      T lv[U][4], rv[U][4], bw[U];
-#pragma unroll
-      for (int k = 0; k < U; ++k) {
-        const int64_t rr = r + (int64_t)k * rs;
-        if (rr < r1) {
-          ldg4(lp[u] + rr * M, lv[k]);
-          ldg4(rp[u] + rr * M, rv[k]);
-          bw[k] = (it_w[u] && a.b) ? __ldg(a.b + rr) : T(1);
-        } else {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) { lv[k][q] = T(0); rv[k][q] = T(0); }
-          bw[k] = T(0);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < U; ++k)
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const A lb = (A)lv[k][p] * (A)bw[k];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) at[u][p * 4 + q] += lb * (A)rv[k][q];
-        }
-    }
-    if (++steps == CHUNK) {
-      steps = 0;
-#pragma unroll
-      for (int u = 0; u < IPT; ++u)
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          neumaier(acc[u][e], cmp[u][e], at[u][e]);
-          at[u][e] = A(0);
-        }
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < IPT; ++u)
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      neumaier(acc[u][e], cmp[u][e], at[u][e]);
-    }
+  const bool weighted = a.b != nullptr;
+  const int boff = a.nsrc * tr * M;
+  const int64_t r0 = (int64_t)blockIdx.x * a.per;
+  const int64_t r1 = min(a.n, r0 + a.per);
+  const int ntiles = r0 < r1 ? (int)((r1 - r0 + tr - 1) / tr) : 0;
   // column sums of R2 (deflation): thread c + ws*g sums rows g, g + ng, ... of column c
-  A cs = A(0);
   const int ng = ws > 0 ? kThreads / ws : 0;
   const int csg = ws > 0 ? threadIdx.x / ws : 0, csc = ws > 0 ? threadIdx.x % ws : 0;
-  if (a.csum && csg < ng) {
-    const T* src = a.R2[csc / M] + csc % M;
-    for (int64_t r = r0 + csg; r < r1; r += ng) cs += (A)__ldg(src + r * M);
+  const bool do_cs = a.csum && csg < ng;
+  const int cso = do_cs ? a.r2map[csc / M] * tr * M + csc % M : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kGramStages; ++s) mbar_init(&full[s], 1);
+    mbar_fence_init();
   }
+  __syncthreads();
+  // thread 0: copy tile t of every source block (and of b) into stage t mod kGramStages
+  auto issue = [&](int t) {
+    const int s = t % kGramStages;
+    const int64_t row = r0 + (int64_t)t * tr;
+    const int rows = (int)min((int64_t)tr, r1 - row);
+    const uint32_t bb = (uint32_t)rows * M * (uint32_t)sizeof(T);
+    const uint32_t wb = weighted ? (((uint32_t)rows * (uint32_t)sizeof(T) + 15u) & ~15u) : 0u;
+    T* dst = reinterpret_cast<T*>(data + (size_t)s * a.stage_bytes);
+    fence_proxy_async();
+    mbar_arrive_expect_tx(&full[s], bb * (uint32_t)a.nsrc + wb);
+    for (int i = 0; i < a.nsrc; ++i) bulk_g2s(dst + (size_t)i * tr * M, a.src[i] + row * M, bb, &full[s]);
+    if (weighted) bulk_g2s(dst + boff, a.b + row, wb, &full[s]);
+  };
+  if (threadIdx.x == 0)
+    for (int t = 0; t < ntiles && t < kGramStages; ++t) issue(t);
+
+  A acc[IPT][16], cmp[IPT][16], at[IPT][16];
+#pragma unroll
+  for (int u = 0; u < IPT; ++u)
+#pragma unroll
+    for (int e = 0; e < 16; ++e) { acc[u][e] = A(0); cmp[u][e] = A(0); at[u][e] = A(0); }
+  constexpr int CHUNK = 16;             // rows summed before the compensated fold
+  int steps = 0;
+  A cs = A(0);
+  int t = 0;
+  bool ok = true;
+  for (; t < ntiles; ++t) {
+    const int s = t % kGramStages;
+    const bool got = mbar_wait(&full[s], (uint32_t)(t / kGramStages) & 1u);
+    if (got) {
+      const T* stg = reinterpret_cast<const T*>(data + (size_t)s * a.stage_bytes);
+      const int rows = (int)min((int64_t)tr, r1 - (r0 + (int64_t)t * tr));
+      if (has_group) {
+#pragma unroll 2
+        for (int r = rg; r < rows; r += rs) {
+          const T bw = weighted ? stg[boff + r] : T(1);
+#pragma unroll
+          for (int u = 0; u < IPT; ++u) {
+            if (!it_ok[u]) continue;
+            T lv[4], rv[4];
+            ld4(stg + lo[u] + r * M, lv);
+            ld4(stg + ro[u] + r * M, rv);
+            const A w = it_w[u] ? (A)bw : A(1);
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+              const A lb = (A)lv[p] * w;
+#pragma unroll
+              for (int q = 0; q < 4; ++q) at[u][p * 4 + q] += lb * (A)rv[q];
+            }
+          }
+          if (++steps == CHUNK) {
+            steps = 0;
+#pragma unroll
+            for (int u = 0; u < IPT; ++u)
+#pragma unroll
+              for (int e = 0; e < 16; ++e) {
+                neumaier(acc[u][e], cmp[u][e], at[u][e]);
+                at[u][e] = A(0);
+              }
+          }
+        }
+      }
+      if (do_cs)
+        for (int r = csg; r < rows; r += ng) cs += (A)stg[cso + r * M];
+    }
+    ok = __syncthreads_and(got) != 0;   // also: every thread is done with stage s
+    if (!ok) break;
+    if (threadIdx.x == 0 && t + kGramStages < ntiles) issue(t + kGramStages);
+  }
+  if (!ok && threadIdx.x == 0) {
+    // a copy did not arrive in time: report it, then wait (bounded) for the copies still
+    // in flight before the stages are reused below; the cluster reduction still runs so
+    // that no peer CTA waits for this one
+    for (int u = t; u < ntiles && u < t + kGramStages; ++u)
+      mbar_wait(&full[u % kGramStages], (uint32_t)(u / kGramStages) & 1u);
+    if (a.st) { a.st->err = MGE_ETIMEOUT; a.st->bad_stage = 5; a.st->done = DONE_ERROR; }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < IPT; ++u)
+#pragma unroll
+    for (int e = 0; e < 16; ++e) neumaier(acc[u][e], cmp[u][e], at[u][e]);
   // CTA reduction: stage [rs][nblk][16], sum over row groups into FP64, then the cluster
   const int len = nblk * 16;
-  A* stage = reinterpret_cast<A*>(smem_raw);
+  A* stage = reinterpret_cast<A*>(data);
   A* cstage = stage + (size_t)rs * len;
-  double* part = reinterpret_cast<double*>(smem_raw + ((((size_t)rs * len + kThreads) * sizeof(A) + 15) / 16) * 16);
+  double* part = reinterpret_cast<double*>(data + ((((size_t)rs * len + kThreads) * sizeof(A) + 15) / 16) * 16);
 #pragma unroll
   for (int u = 0; u < IPT; ++u)
     if (it_ok[u]) {
-      int item = ti + u * tpi;
+      const int item = ti + u * tpi;
 #pragma unroll
       for (int e = 0; e < 16; ++e) stage[(size_t)rg * len + item * 16 + e] = acc[u][e] + cmp[u][e];
     }
-  if (a.csum) cstage[threadIdx.x] = (csg < ng) ? cs : A(0);
+  if (a.csum) cstage[threadIdx.x] = do_cs ? cs : A(0);
   __syncthreads();
-  for (int t = threadIdx.x; t < len; t += kThreads) {
-    double s = 0.0;
-    for (int g = 0; g < rs; ++g) s += (double)stage[(size_t)g * len + t];
-    part[t] = s;
+  // row groups summed in the accumulator precision (compensated), one conversion per entry
+  for (int i = threadIdx.x; i < len; i += kThreads) {
+    A sum = A(0), c = A(0);
+    for (int g = 0; g < rs; ++g) neumaier(sum, c, stage[(size_t)g * len + i]);
+    part[i] = (double)sum + (double)c;
   }
   if (a.csum && threadIdx.x < ws) {
-    double s = 0.0;
-    for (int g = 0; g < ng; ++g) s += (double)cstage[g * ws + threadIdx.x];
-    part[len + threadIdx.x] = s;
+    A sum = A(0), c = A(0);
+    for (int g = 0; g < ng; ++g) neumaier(sum, c, cstage[g * ws + threadIdx.x]);
+    part[len + threadIdx.x] = (double)sum + (double)c;
   }
   const int tot = len + (a.csum ? ws : 0);
-  const int cl = cluster_id();
   // each cluster adds its total into the single accumulator the consumer reads (and zeroes)
-  (void)cl;
-  cluster_sum(part, tot, [&](int t, double v) {
-    if (t >= len) { atomicAdd(a.csum + (t - len), v); return; }
-    int item = t / 16, e = t % 16, p = e / 4, q = e % 4;
+  cluster_sum(part, tot, [&](int i, double v) {
+    if (i >= len) { atomicAdd(a.csum + (i - len), v); return; }
+    int item = i / 16, e = i % 16, p = e / 4, q = e % 4;
     int prod, bi, bj;
     decode_item(item, nb1, b1, bl, a.sym2, b2, prod, bi, bj);
     if (prod == 1) atomicAdd(a.out1 + (bi * 4 + p) * MAXS + bj * 4 + q, v);
@@ -651,7 +671,8 @@ struct Solver {
     return MGE_OK;
   }
 
-  size_t gram_smem(int nl, int n1, int n2, bool sym2, bool csum) {
+  // shared memory of the Gram epilogue (row-group stage, column-sum stage, FP64 partials)
+  size_t gram_epi_bytes(int nl, int n1, int n2, bool sym2, bool csum) const {
     int bl = nl * M / 4;
     int nblk = bl * (n1 * M / 4) + (sym2 ? bl * (bl + 1) / 2 : bl * (n2 * M / 4));
     int rs = std::max(1, kThreads / nblk);
@@ -663,17 +684,32 @@ struct Solver {
                    bool sym2, bool weighted, double* out1, double* out2, int ld2, int stride2, bool csum) {
     GramArgs<T> g{};
     g.n = n; g.nl = nl; g.n1 = n1; g.n2 = n2;
-    for (int i = 0; i < 3; ++i) {
-      g.L[i] = i < nl ? L[i] : nullptr;
-      g.R1[i] = i < n1 ? R1[i] : nullptr;
-      g.R2[i] = i < n2 ? R2[i] : nullptr;
-    }
     g.sym2 = sym2;
     g.b = weighted ? static_cast<const T*>(op.b) : nullptr;
     g.out1 = out1; g.out2 = out2; g.ld2 = ld2; g.stride2 = stride2;
     g.csum = csum ? &sm->partC[0][0] : nullptr;
     g.st = state;
-    size_t smem = gram_smem(nl, n1, n2, sym2, csum);
+    auto source = [&g](const T* p) {
+      for (int i = 0; i < g.nsrc; ++i)
+        if (g.src[i] == p) return i;
+      g.src[g.nsrc] = p;
+      return g.nsrc++;
+    };
+    for (int i = 0; i < nl; ++i) g.lmap[i] = source(L[i]);
+    for (int i = 0; i < n1; ++i) g.r1map[i] = source(R1[i]);
+    if (!sym2)
+      for (int i = 0; i < n2; ++i) g.r2map[i] = source(R2[i]);
+    auto stage_bytes = [&](int tr) {
+      size_t b = (size_t)g.nsrc * tr * M * sizeof(T) + (weighted ? ((tr * sizeof(T) + 15) / 16) * 16 : 0);
+      return ((b + 127) / 128) * 128;
+    };
+    int tr = 64;
+    while (tr > 16 && stage_bytes(tr) > 24576) tr /= 2;
+    g.tr = tr;
+    g.stage_bytes = (uint32_t)stage_bytes(tr);
+    int64_t per = (n + grid_gram - 1) / grid_gram;
+    g.per = ((per + tr - 1) / tr) * tr;
+    size_t smem = 128 + std::max((size_t)kGramStages * g.stage_bytes, gram_epi_bytes(nl, n1, n2, sym2, csum));
     k_gram<T, M><<<grid_gram, kThreads, smem, st>>>(g);
     MGE_LAUNCHED(ctx, 1);
   }

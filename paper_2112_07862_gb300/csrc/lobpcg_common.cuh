@@ -42,7 +42,6 @@ struct Small {
   double partN[MAXCL][2 * MAXM];      // ||r_k||^2 and ||x_k||^2, per cluster
   double Cx[MAXS * MAXM], Cp[MAXS * MAXM];
   double lam[MAXM];
-  double Linv[MAXM * MAXM], Mx[MAXM * MAXM], Mp[MAXM * MAXM], cmean[MAXM];
   unsigned long long vmax[MAXM];
   unsigned long long vidx[MAXM];
 };
@@ -52,7 +51,9 @@ template <typename T>
 struct SmallT {
   T Cx[MAXS * MAXM], Cp[MAXS * MAXM];
   T lam[MAXM];
-  T Linv[MAXM * MAXM], Mx[MAXM * MAXM], Mp[MAXM * MAXM], cmean[MAXM];
+  // W normalisation L (upper triangular, right factor) and the products the SpMM epilogue
+  // applies: W = W_raw L - X (M_x L) - P (M_p L) - 1 (c L)
+  T Linv[MAXM * MAXM], MxL[MAXM * MAXM], MpL[MAXM * MAXM], cL[MAXM];
 };
 
 // ---- 4-wide vector access -------------------------------------------------------------
@@ -102,6 +103,43 @@ __device__ __forceinline__ void cluster_sum(const double* buf, int len, F store)
 }
 
 __device__ __forceinline__ int cluster_id() { return blockIdx.x / CL; }
+
+// ---- bulk asynchronous copies (TMA, 1-D) and mbarriers -----------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make initialised barriers visible to the asynchronous (copy) proxy
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> this CTA's shared memory; dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return done != 0;
+}
+// Waits for the phase with the given parity to complete; gives up (false) after about
+// max_cycles SM cycles so that a lost copy cannot hang the GPU.
+constexpr long long kWaitCycles = 1ll << 31;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long max_cycles = kWaitCycles) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > max_cycles) return false;
+  return true;
+}
 
 // Sum of p[c * stride] for c < n with eight loads in flight (the partial sums sit in L2; a
 // plain dependent loop pays the full load latency per term).

@@ -613,9 +613,9 @@ __global__ void __launch_bounds__(kRWThreads) k_rr_warp(RRArgs a) {
   __shared__ float sU[WN][MAXM + 1];
   __shared__ float sV[WN][MAXM + 1];
   __shared__ float sgp[MAXM][MAXM + 1];
-  __shared__ double sdsc[WN];
+  __shared__ float sdf[WN];             // scaling D (unit G_A diagonal)
   __shared__ float srd[WN], sd[WN], se[WN], se2[WN], sht[WN], sp[WN], smu[MAXM], srdp[MAXM];
-  __shared__ int sidx[WN];
+  __shared__ int sidx[WN], sinv[WN];    // compact -> full index, full -> compact (-1: dropped)
   __shared__ unsigned slive;
   Small* sm = a.sm;
   if (threadIdx.x < 12) sclk[threadIdx.x] = 0;
@@ -626,25 +626,28 @@ __global__ void __launch_bounds__(kRWThreads) k_rr_warp(RRArgs a) {
     const double gaii = sm->partA[0][li * MAXS + li], gbii = sm->partB[0][li * MAXS + li];
     const bool live = lane < n && gaii > 1e-30 && gbii > 1e-30 && gaii < 1e30 && gbii < 1e30;
     // any positive scaling is exact enough: it is undone in C_x and C_p with the same factors
-    sdsc[lane] = live ? (double)rsqrtf((float)gaii) : 0.0;
+    sdf[lane] = live ? rsqrtf((float)gaii) : 0.f;
     const unsigned lm = __ballot_sync(0xffffffffu, live);
     slive = lm;
   }
   __syncthreads();
+  // each FP64 partial is rounded to FP32 once (GB300's FP64 rate is a small fraction of its
+  // FP32 rate); G_B holds only its block-upper part
   int bad = 0;
   for (int t = threadIdx.x; t < WN * WN; t += kRWThreads) {
     const int i = t >> 5, j = t & 31;
-    const bool in = i < n && j < n;
-    const int ii = in ? i : 0, jj = in ? j : 0;
-    const double ga = 0.5 * (sm->partA[0][ii * MAXS + jj] + sm->partA[0][jj * MAXS + ii]);
-    const int bi = ii / 4, bj = jj / 4;
-    const double gb = (bi < bj) ? sm->partB[0][ii * MAXS + jj]
-                    : (bi > bj) ? sm->partB[0][jj * MAXS + ii]
-                                : 0.5 * (sm->partB[0][ii * MAXS + jj] + sm->partB[0][jj * MAXS + ii]);
-    bad |= in && !(isfinite(ga) && isfinite(gb));
-    const float sc = (float)sdsc[i] * (float)sdsc[j];
-    sA[i][j] = in ? (float)ga * sc : 0.f;
-    sB[i][j] = in ? (float)gb * sc : 0.f;
+    float ga = 0.f, gb = 0.f;
+    if (i < n && j < n) {
+      const int bi = i / 4, bj = j / 4;
+      ga = 0.5f * ((float)sm->partA[0][i * MAXS + j] + (float)sm->partA[0][j * MAXS + i]);
+      const float b1 = (bi <= bj) ? (float)sm->partB[0][i * MAXS + j] : 0.f;
+      const float b2 = (bi >= bj) ? (float)sm->partB[0][j * MAXS + i] : 0.f;
+      gb = (bi < bj) ? b1 : (bi > bj) ? b2 : 0.5f * (b1 + b2);
+      bad |= !(isfinite(ga) && isfinite(gb));
+    }
+    const float sc = sdf[i] * sdf[j];
+    sA[i][j] = ga * sc;
+    sB[i][j] = gb * sc;
   }
   bad = __syncthreads_or(bad);
   for (int t = threadIdx.x; t < n * n; t += kRWThreads) {      // the next Gram starts from zero
@@ -686,6 +689,7 @@ __global__ void __launch_bounds__(kRWThreads) k_rr_warp(RRArgs a) {
     const bool kept = (keep >> i) & 1u;
     const int pos = __popc(keep & ((1u << i) - 1u));
     sidx[kept ? pos : k + (i - pos)] = kept ? i : 0;
+    sinv[i] = kept ? pos : -1;
   }
   RW_MARK(9);
   if (k < M) {
@@ -963,17 +967,24 @@ __global__ void __launch_bounds__(kRWThreads) k_rr_warp(RRArgs a) {
     for (int s_ = 0; s_ < k; ++s_) v += sL[s_][r] * sZ[s_][q];
     sU[r][q] = v;
   }
-  for (int t = threadIdx.x; t < MAXS * MAXM; t += kRWThreads) { sm->Cx[t] = 0.0; sm->Cp[t] = 0.0; }
   const int badmu = __syncthreads_or(threadIdx.x < M && !(smu[threadIdx.x] > 0.f && isfinite(smu[threadIdx.x])));
   if (badmu) {
     if (threadIdx.x == 0) { a.st->done = DONE_ERROR; a.st->err = MGE_ENOTFINITE; a.st->bad_stage = 4; }
     return;
   }
-  for (int t = threadIdx.x; t < k * M; t += kRWThreads) {
-    const int r = t / M, q = t % M;
-    sm->Cx[sidx[r] * MAXM + q] = sdsc[sidx[r]] * (double)(sU[r][q] * rsqrtf(smu[q]));
+  // the coefficients go straight into the block-precision copies the update kernel reads
+  // (this form runs for FP32 blocks only); rows of dropped directions are zero
+  SmallT<float>* cf = static_cast<SmallT<float>*>(a.smt);
+  for (int t = threadIdx.x; t < n * M; t += kRWThreads) {
+    const int i = t / M, q = t % M, r = sinv[i];
+    cf->Cx[i * MAXM + q] = r >= 0 ? sdf[i] * (sU[r][q] * rsqrtf(smu[q])) : 0.f;
+    if (nx == 0) cf->Cp[i * MAXM + q] = 0.f;
   }
-  if (threadIdx.x < M) sm->lam[threadIdx.x] = 1.0 / (double)smu[threadIdx.x];
+  if (threadIdx.x < M) {
+    const double lam = 1.0 / (double)smu[threadIdx.x];
+    sm->lam[threadIdx.x] = lam;
+    cf->lam[threadIdx.x] = (float)lam;
+  }
   RW_MARK(8);
 
   // ---- 9. C_p: in u = L^T z coordinates the G_B inner product is u^T M u'; the Ritz vectors
@@ -1076,20 +1087,19 @@ __global__ void __launch_bounds__(kRWThreads) k_rr_warp(RRArgs a) {
       }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < k * M; t += kRWThreads) {     // z_p = L^-T u, C_p = D z_p
-      const int r = t / M, q = t % M;
+    for (int t = threadIdx.x; t < n * M; t += kRWThreads) {     // z_p = L^-T u, C_p = D z_p
+      const int i = t / M, q = t % M, r = sinv[i];
       float v0 = 0.f, v1 = 0.f;
+      if (r >= 0) {
 #pragma unroll
-      for (int s_ = 0; s_ < WN; s_ += 2) {
-        v0 += sL[s_][r] * sU[s_][q];
-        v1 += sL[s_ + 1][r] * sU[s_ + 1][q];
+        for (int s_ = 0; s_ < WN; s_ += 2) {
+          v0 += sL[s_][r] * sU[s_][q];
+          v1 += sL[s_ + 1][r] * sU[s_ + 1][q];
+        }
       }
-      sm->Cp[sidx[r] * MAXM + q] = sdsc[sidx[r]] * (double)(v0 + v1);
+      cf->Cp[i * MAXM + q] = sdf[i] * (v0 + v1);
     }
   }
-  __syncthreads();
-  if (a.is_double) store_coeffs<double, float>(a);
-  else store_coeffs<float, float>(a);
   RW_MARK(11);
   __syncthreads();
   if (threadIdx.x < 12) a.st->rr_clk[threadIdx.x] = sclk[threadIdx.x];
@@ -1349,6 +1359,31 @@ __global__ void __launch_bounds__(kThreads) k_rr_jacobi(RRArgs a) {
   if (threadIdx.x == 0) a.st->kept = k;
 }
 
+// Same factorisation for n <= 32 by one warp (lane = row, columns broadcast by shuffles);
+// called by the whole warp, no block barrier.
+template <typename R>
+__device__ void chol_drop_warp(R* S, int ld, int n, const R* tau, int* keep, R* rd) {
+  const int i = threadIdx.x & 31;
+  const int ri = i < n ? i : 0;
+  for (int j = 0; j < n; ++j) {
+    const R v = S[j * ld + j];
+    const bool ok = keep[j] && v > tau[j] && isfinite((double)v);
+    const R piv = ok ? (R)sqrt(v) : R(0);
+    const R rp = ok ? R(1) / piv : R(0);
+    const R lij = (i > j && i < n) ? S[ri * ld + j] * rp : R(0);
+    __syncwarp();
+    for (int k = j + 1; k < n; ++k) {
+      const R lkj = __shfl_sync(0xffffffffu, lij, k);
+      if (k <= i && i < n) S[ri * ld + k] -= lij * lkj;
+    }
+    if (i == j) { S[j * ld + j] = piv; rd[j] = rp; keep[j] = ok ? 1 : 0; }
+    if (i > j && i < n) S[ri * ld + j] = lij;
+    __syncwarp();
+  }
+  for (int k = i + 1; k < n; ++k) S[ri * ld + k] = R(0);
+  __syncwarp();
+}
+
 // ---------------------------------------------------------------------------------------
 // wprep: backward errors and convergence; projections Mx, Mp and the normalisation of the
 // projected W_raw (Cholesky with dropping, in R precision)
@@ -1358,47 +1393,54 @@ __global__ void __launch_bounds__(kThreads) k_wprep(WprepArgs a) {
   if (a.st->done) return;
   const int M = a.M;
   Small* sm = a.sm;
-  __shared__ double G2[MAXS * MAXM];
-  __shared__ double cs[MAXM];
+  // The FP64 Gram partials are rounded to R once; everything after runs in R (FP32 for FP32
+  // blocks: GB300's FP64 rate is a small fraction of its FP32 rate, conversions included).
+  __shared__ R G2[MAXS * MAXM];
+  __shared__ R cs[MAXM];
   __shared__ R G[MAXM * (MAXM + 1)];
   __shared__ R tau[MAXM], rdw[MAXM];
+  __shared__ R sLinv[MAXM][MAXM + 1];
   __shared__ int keep[MAXM];
-  __shared__ int conv_all, bad, bad_g;
+  __shared__ long long sclk[4];
+  // phase clocks written by every thread (a branch around clock64 leaves warps diverged)
+  const long long clk0 = clock64();
+#define WP_MARK(k) (sclk[k] = clock64() - clk0)
   const int ld = M + 1;
   const int rows = (a.has_x ? M : 0) + (a.has_p ? M : 0) + M;
-  long long clk0 = clock64();
-  if (threadIdx.x == 0) { conv_all = 1; bad = 0; bad_g = 0; }
-  // sum the W-side Gram partials and the column sums
   for (int t = threadIdx.x; t < rows * M; t += blockDim.x) {
     int i = t / M, j = t % M;
-    G2[i * MAXM + j] = sum_strided(&sm->partW[0][i * MAXM + j], a.ncl_w, MAXS * MAXM);
+    const double v = a.ncl_w == 1 ? sm->partW[0][i * MAXM + j] : sum_strided(&sm->partW[0][i * MAXM + j], a.ncl_w, MAXS * MAXM);
+    G2[i * MAXM + j] = (R)v;
   }
   for (int t = threadIdx.x; t < M; t += blockDim.x) {
-    cs[t] = a.deflate ? sum_strided(&sm->partC[0][t], a.ncl_w, MAXM) : 0.0;
+    const double v = !a.deflate ? 0.0 : a.ncl_w == 1 ? sm->partC[0][t] : sum_strided(&sm->partC[0][t], a.ncl_w, MAXM);
+    cs[t] = (R)v;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) a.st->wp_clk[0] = clock64() - clk0;
+  int bad = 0, unconv = 0;
   if (a.check) {
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
-      double rn2 = sum_strided(&sm->partN[0][k], a.ncl_n, 2 * MAXM);
-      double xn2 = sum_strided(&sm->partN[0][MAXM + k], a.ncl_n, 2 * MAXM);
-      double lam = sm->lam[k];
-      double eta = sqrt(rn2) / ((a.norm + fabs(lam) * a.bmax) * sqrt(xn2));
-      if (!isfinite(eta) || !isfinite(lam)) bad = 1;
-      a.st->eta[k] = eta;
+      const double rn2 = a.ncl_n == 1 ? sm->partN[0][k] : sum_strided(&sm->partN[0][k], a.ncl_n, 2 * MAXM);
+      const double xn2 = a.ncl_n == 1 ? sm->partN[0][MAXM + k] : sum_strided(&sm->partN[0][MAXM + k], a.ncl_n, 2 * MAXM);
+      const double lam = sm->lam[k];
+      // backward error; FP32 arithmetic is ample for a number compared with a tolerance
+      const float eta = sqrtf((float)rn2) / (((float)a.norm + fabsf((float)lam) * (float)a.bmax) * sqrtf((float)xn2));
+      bad |= !isfinite(eta) || !isfinite(lam);
+      a.st->eta[k] = (double)eta;
       a.st->lambda[k] = lam;
-      if (k < a.K && !(eta <= a.tol)) conv_all = 0;
+      unconv |= k < a.K && !(eta <= (float)a.tol);
     }
   }
-  __syncthreads();
+  bad = __syncthreads_or(bad);
+  unconv = __syncthreads_or(unconv);
+  WP_MARK(0);
   if (a.check && threadIdx.x == 0) {
     a.st->iter += 1;
     if (bad) { a.st->done = DONE_ERROR; a.st->err = MGE_ENOTFINITE; a.st->bad_stage = 2; }
-    else if (conv_all) a.st->done = DONE_CONVERGED;
+    else if (!unconv) a.st->done = DONE_CONVERGED;
     else if (a.st->iter >= a.maxiter) a.st->done = DONE_MAXITER;
   }
   const int ox = 0, op = a.has_x ? M : 0, ow = (a.has_x ? M : 0) + (a.has_p ? M : 0);
-  const double inv_n = 1.0 / (double)a.n;
+  const R inv_n = (R)(1.0 / (double)a.n);
   // the accumulators start the next reduction from zero (everything was read above)
   for (int t = threadIdx.x; t < rows * M; t += blockDim.x) {
     int i = t / M, j = t % M;
@@ -1408,60 +1450,78 @@ __global__ void __launch_bounds__(kThreads) k_wprep(WprepArgs a) {
     for (int c = 0; c < a.ncl_w; ++c) sm->partC[c][t] = 0.0;
     for (int c = 0; c < a.ncl_n; ++c) { sm->partN[c][t] = 0.0; sm->partN[c][MAXM + t] = 0.0; }
   }
+  int bad_g = 0;
   for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
     int i = t / M, j = t % M;
-    // R-precision subtraction: entries below tau_w * G_jj are dropped anyway
-    R g = (R)(0.5 * (G2[(ow + i) * MAXM + j] + G2[(ow + j) * MAXM + i]));
+    // G_W - M_x^T M_x - M_p^T M_p - n c c^T: entries below tau_w * G_jj are dropped anyway
+    R g = R(0.5) * (G2[(ow + i) * MAXM + j] + G2[(ow + j) * MAXM + i]);
     for (int l = 0; l < M; ++l) {
-      if (a.has_x) g -= (R)G2[(ox + l) * MAXM + i] * (R)G2[(ox + l) * MAXM + j];
-      if (a.has_p) g -= (R)G2[(op + l) * MAXM + i] * (R)G2[(op + l) * MAXM + j];
+      if (a.has_x) g -= G2[(ox + l) * MAXM + i] * G2[(ox + l) * MAXM + j];
+      if (a.has_p) g -= G2[(op + l) * MAXM + i] * G2[(op + l) * MAXM + j];
     }
-    if (a.deflate) g -= (R)(cs[i] * cs[j] * inv_n);
+    if (a.deflate) g -= cs[i] * cs[j] * inv_n;
     G[i * ld + j] = g;
-    if (!isfinite((double)g)) bad_g = 1;
-  }
-  for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
-    int i = t / M, j = t % M;
-    sm->Mx[i * MAXM + j] = a.has_x ? G2[(ox + i) * MAXM + j] : 0.0;
-    sm->Mp[i * MAXM + j] = a.has_p ? G2[(op + i) * MAXM + j] : 0.0;
+    bad_g |= !isfinite(g);
   }
   for (int t = threadIdx.x; t < M; t += blockDim.x) {
-    double g0 = G2[(ow + t) * MAXM + t];
-    tau[t] = (R)(a.tau_w * g0);
-    keep[t] = (g0 > 0.0 && isfinite(g0)) ? 1 : 0;
-    sm->cmean[t] = cs[t] * inv_n;
+    const R g0 = G2[(ow + t) * MAXM + t];
+    tau[t] = (R)a.tau_w * g0;
+    keep[t] = (g0 > R(0) && isfinite(g0)) ? 1 : 0;
   }
-  __syncthreads();
+  bad_g = __syncthreads_or(bad_g);
   if (bad_g) {
     if (threadIdx.x == 0) { a.st->done = DONE_ERROR; a.st->err = MGE_ENOTFINITE; a.st->bad_stage = 3; }
     return;
   }
-  if (threadIdx.x == 0) a.st->wp_clk[1] = clock64() - clk0;
-  chol_drop<R>(G, ld, M, tau, keep, rdw);
-  if (threadIdx.x == 0) a.st->wp_clk[2] = clock64() - clk0;
-  // Linv = L^-T (upper triangular); column c solves L^T y = e_c
+  WP_MARK(1);
+  if (threadIdx.x < 32) chol_drop_warp<R>(G, ld, M, tau, keep, rdw);
+  __syncthreads();
+  WP_MARK(2);
+  // L = L_G^-T (upper triangular): column c solves L_G^T y = e_c, y in registers
   for (int c = threadIdx.x; c < M; c += blockDim.x) {
     R y[MAXM];
-    for (int r = M - 1; r >= 0; --r) {
-      if (!(rdw[r] > R(0))) { y[r] = R(0); continue; }
+#pragma unroll
+    for (int r = MAXM - 1; r >= 0; --r) {
       R v = (r == c) ? R(1) : R(0);
-      for (int s = r + 1; s < M; ++s) v -= G[s * ld + r] * y[s];
-      y[r] = v * rdw[r];
+#pragma unroll
+      for (int s_ = r + 1; s_ < MAXM; ++s_)
+        if (s_ < M) v -= G[s_ * ld + r] * y[s_];
+      y[r] = (r < M && rdw[r] > R(0)) ? v * rdw[r] : R(0);
     }
-    for (int r = 0; r < M; ++r) sm->Linv[r * MAXM + c] = (double)y[r];
+#pragma unroll
+    for (int r = 0; r < MAXM; ++r)
+      if (r < M) sLinv[r][c] = y[r];
   }
   __syncthreads();
-  if (a.is_double) {
-    SmallT<double>* o = static_cast<SmallT<double>*>(a.smt);
-    for (int t = threadIdx.x; t < MAXM * MAXM; t += blockDim.x) { o->Linv[t] = sm->Linv[t]; o->Mx[t] = sm->Mx[t]; o->Mp[t] = sm->Mp[t]; }
-    for (int t = threadIdx.x; t < MAXM; t += blockDim.x) o->cmean[t] = sm->cmean[t];
-  } else {
-    SmallT<float>* o = static_cast<SmallT<float>*>(a.smt);
-    for (int t = threadIdx.x; t < MAXM * MAXM; t += blockDim.x) { o->Linv[t] = (float)sm->Linv[t]; o->Mx[t] = (float)sm->Mx[t]; o->Mp[t] = (float)sm->Mp[t]; }
-    for (int t = threadIdx.x; t < MAXM; t += blockDim.x) o->cmean[t] = (float)sm->cmean[t];
+  // publish L and the products the SpMM epilogue applies: M_x L, M_p L with
+  // M_x = X^T B W_raw, M_p = P^T B W_raw, and c L with c the column means of W_raw
+  for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
+    const int i = t / M, c = t % M;
+    R mxl = R(0), mpl = R(0);
+    for (int l = 0; l < M; ++l) {
+      if (a.has_x) mxl += G2[(ox + i) * MAXM + l] * sLinv[l][c];
+      if (a.has_p) mpl += G2[(op + i) * MAXM + l] * sLinv[l][c];
+    }
+    const int o = i * MAXM + c;
+    if (a.is_double) {
+      SmallT<double>* d = static_cast<SmallT<double>*>(a.smt);
+      d->Linv[o] = (double)sLinv[i][c]; d->MxL[o] = (double)mxl; d->MpL[o] = (double)mpl;
+    } else {
+      SmallT<float>* f = static_cast<SmallT<float>*>(a.smt);
+      f->Linv[o] = (float)sLinv[i][c]; f->MxL[o] = (float)mxl; f->MpL[o] = (float)mpl;
+    }
   }
+  for (int c = threadIdx.x; c < M; c += blockDim.x) {
+    R cl = R(0);
+    if (a.deflate)
+      for (int l = 0; l < M; ++l) cl += cs[l] * inv_n * sLinv[l][c];
+    if (a.is_double) static_cast<SmallT<double>*>(a.smt)->cL[c] = (double)cl;
+    else static_cast<SmallT<float>*>(a.smt)->cL[c] = (float)cl;
+  }
+  WP_MARK(3);
   __syncthreads();
-  if (threadIdx.x == 0) a.st->wp_clk[3] = clock64() - clk0;
+  if (threadIdx.x < 4) a.st->wp_clk[threadIdx.x] = sclk[threadIdx.x];
+#undef WP_MARK
 }
 
 // ---------------------------------------------------------------------------------------
