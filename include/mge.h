@@ -109,6 +109,8 @@ typedef struct {
   int      eps_maxiter;       /* default 20000                                              */
   uint64_t seed;              /* seed of the eps solve's initial block                      */
   void*    stream;            /* cudaStream_t or NULL                                       */
+  int      eps_precond_degree; /* Chebyshev preconditioner degree of the eps solve (see
+                                 mge_embed_opts.precond_degree; 0 = default 12)              */
 } mge_ops_opts;
 
 /* Builds the operators of Sec. 4 for the graph W (n nodes, CSR as described above; host
@@ -197,6 +199,14 @@ typedef struct {
   int         x0_on_device;
   int         v_on_device;    /* V is a device pointer                                      */
   void*       stream;         /* cudaStream_t or NULL                                       */
+  int         precond_degree; /* LOBPCG preconditioner: the residual block R becomes
+                                 p(D^-1 A) D^-1 R, p the degree-d Chebyshev iteration for
+                                 A y = R on [beta / (2 d^2), beta], D = diag(A), beta the
+                                 Gershgorin bound of D^-1 A.  d = 1 is the Jacobi
+                                 preconditioner; each degree above 1 costs one SpMM per
+                                 iteration and cuts the iteration count about in proportion.
+                                 The paper leaves the preconditioner open.  0 = default 12;
+                                 at most 64.                                                */
 } mge_embed_opts;
 
 typedef struct {

@@ -217,13 +217,13 @@ static LobOp make_op(const Ops& op, int which, int precision) {
     l.shift = op.eps;
     l.b = dbl ? (const void*)op.b.p : (const void*)op.b32.p;
     l.dinv = dbl ? (const void*)op.dinv_a.p : (const void*)op.dinv_a32.p;
-    l.norm = op.norm_a; l.bmax = op.bmax; l.deflate = false;
+    l.norm = op.norm_a; l.bmax = op.bmax; l.deflate = false; l.beta = op.beta_a;
   } else {
     l.ptr = op.q_ptr.p; l.col = op.q_col.p;
     l.val = dbl ? (const void*)op.q_val.p : (const void*)op.q_val32.p;
     l.shift = 0.0; l.b = nullptr;
     l.dinv = dbl ? (const void*)op.dinv_q.p : (const void*)op.dinv_q32.p;
-    l.norm = op.norm_q; l.bmax = 1.0; l.deflate = true;
+    l.norm = op.norm_q; l.bmax = 1.0; l.deflate = true; l.beta = op.beta_q;
   }
   return l;
 }
@@ -309,6 +309,7 @@ mge_status mge_embed(mge_ctx* c, const mge_ops* o, int K, double tol, const mge_
     else { MGE_TRY(vd.alloc(ctx, (size_t)op.n * K)); vout = vd.p; }
   }
   LobResult r;
+  l.precond_degree = e.precond_degree > 0 ? std::min(e.precond_degree, 64) : kDefaultPrecondDegree;
   mge_status s = lobpcg_solve(ctx, st, l, prec, K, m, tol, e.maxiter, e.seed, e.check_every, e.use_graph != 0,
                               x0, x0c, vout, &r);
   if (s != MGE_OK && s != MGE_ENOTCONVERGED) {

@@ -322,7 +322,7 @@ __global__ void k_fill_q(int64_t n, const int32_t* __restrict__ T, const int64_t
                          const int32_t* __restrict__ tlist, const int64_t* __restrict__ qp,
                          int32_t* __restrict__ qc, double* __restrict__ qv, float* __restrict__ qv32,
                          double* __restrict__ dinv, float* __restrict__ dinv32, double* den_max,
-                         double* norm_max) {
+                         double* norm_max, double* beta_max) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int Ti = T[i];
@@ -347,6 +347,8 @@ __global__ void k_fill_q(int64_t n, const int32_t* __restrict__ T, const int64_t
   atomic_max_nonneg(norm_max, diag - offsum);
   double d = diag > 0 ? 1.0 / diag : 1.0;
   dinv[i] = d; dinv32[i] = (float)d;
+  // Gershgorin bound of the spectrum of D^-1 Q (the polynomial preconditioner's interval)
+  if (diag > 0) atomic_max_nonneg(beta_max, (diag - offsum) * d);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -484,7 +486,7 @@ __global__ void k_finish_a(int64_t n, const int64_t* __restrict__ ap, const int3
                            const double* __restrict__ av, const double* __restrict__ r,
                            const double* __restrict__ sumlog, double* __restrict__ b,
                            float* __restrict__ b32, double* __restrict__ dinv, float* __restrict__ dinv32,
-                           float* __restrict__ av32, double* norm_max, double* bmax) {
+                           float* __restrict__ av32, double* norm_max, double* bmax, double* beta_max) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double g = exp(*sumlog / (double)n);
@@ -499,6 +501,8 @@ __global__ void k_finish_a(int64_t n, const int64_t* __restrict__ ap, const int3
   dinv[i] = d; dinv32[i] = (float)d;
   atomic_max_nonneg(norm_max, fmax(aii + r[i], 0.0));
   atomic_max_nonneg(bmax, bi);
+  // Gershgorin bound of the spectrum of D^-1 A (the polynomial preconditioner's interval)
+  if (aii > 0) atomic_max_nonneg(beta_max, (aii + r[i]) * d);
 }
 
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
@@ -567,6 +571,8 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
   double* norma = d_sc.p + 2;
   double* bmax = d_sc.p + 3;
   double* sumlog = d_sc.p + 4;
+  double* beta_q = d_sc.p + 5;
+  double* beta_a = d_sc.p + 6;
 
   const int B = 256;
   // structure first; the symmetry check indexes rows by column values, so it runs only on a
@@ -625,8 +631,12 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
   DevBuf<int64_t> qcnt, acnt;
   MGE_TRY(qcnt.alloc(ctx, n));
   MGE_TRY(acnt.alloc(ctx, n));
-  MGE_TRY(ops->q_ptr.alloc(ctx, n + 1));
-  MGE_TRY(ops->a_ptr.alloc(ctx, n + 1));
+  // CSR arrays carry a few zeroed elements past their ends: the LOBPCG SpMM copies row
+  // pointers, column indices and values in tiles whose byte counts are rounded up to 16
+  MGE_TRY(ops->q_ptr.alloc(ctx, n + 2));
+  MGE_TRY(ops->a_ptr.alloc(ctx, n + 2));
+  MGE_CUDA(ctx, cudaMemsetAsync(ops->q_ptr.p + n + 1, 0, sizeof(int64_t), st));
+  MGE_CUDA(ctx, cudaMemsetAsync(ops->a_ptr.p + n + 1, 0, sizeof(int64_t), st));
   k_counts<<<grid_for(n, B), B, 0, st>>>(n, rp, ops->T.p, qcnt.p, acnt.p);
   MGE_LAUNCHED(ctx, 1);
   MGE_TRY(exclusive_scan(ctx, st, qcnt.p, n, ops->q_ptr.p));
@@ -636,14 +646,19 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
   MGE_CUDA(ctx, cudaStreamSynchronize(st));
 
   // --- Q values, Eq. 9 denominators, preconditioner ---
-  MGE_TRY(ops->q_col.alloc(ctx, ops->nnz_q));
-  MGE_TRY(ops->q_val.alloc(ctx, ops->nnz_q));
-  MGE_TRY(ops->q_val32.alloc(ctx, ops->nnz_q));
-  MGE_TRY(ops->dinv_q.alloc(ctx, n));
-  MGE_TRY(ops->dinv_q32.alloc(ctx, n));
+  MGE_TRY(ops->q_col.alloc(ctx, ops->nnz_q + 4));
+  MGE_TRY(ops->q_val.alloc(ctx, ops->nnz_q + 4));
+  MGE_TRY(ops->q_val32.alloc(ctx, ops->nnz_q + 4));
+  MGE_CUDA(ctx, cudaMemsetAsync(ops->q_col.p + ops->nnz_q, 0, 4 * sizeof(int32_t), st));
+  MGE_CUDA(ctx, cudaMemsetAsync(ops->q_val.p + ops->nnz_q, 0, 4 * sizeof(double), st));
+  MGE_CUDA(ctx, cudaMemsetAsync(ops->q_val32.p + ops->nnz_q, 0, 4 * sizeof(float), st));
+  MGE_TRY(ops->dinv_q.alloc(ctx, n + 4));
+  MGE_CUDA(ctx, cudaMemsetAsync(ops->dinv_q.p + n, 0, 4 * sizeof(double), st));
+  MGE_TRY(ops->dinv_q32.alloc(ctx, n + 4));
+  MGE_CUDA(ctx, cudaMemsetAsync(ops->dinv_q32.p + n, 0, 4 * sizeof(float), st));
   k_fill_q<<<grid_for(n, B), B, 0, st>>>(n, ops->T.p, U.p, tlist.p, ops->q_ptr.p, ops->q_col.p,
                                           ops->q_val.p, ops->q_val32.p, ops->dinv_q.p, ops->dinv_q32.p,
-                                          den_max, normq);
+                                          den_max, normq, beta_q);
   MGE_LAUNCHED(ctx, 1);
 
   // --- components of the two-hop graph (eps = 0 when more than one) ---
@@ -656,7 +671,8 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
     MGE_LAUNCHED(ctx, 3);
     MGE_CUDA(ctx, cudaGetLastError());
     int h_ncomp = 0;
-    double h_den = 0, h_nq = 0;
+    double h_den = 0, h_nq = 0, h_bq = 0;
+    MGE_CUDA(ctx, cudaMemcpyAsync(&h_bq, beta_q, sizeof(double), cudaMemcpyDeviceToHost, st));
     MGE_CUDA(ctx, cudaMemcpyAsync(&h_ncomp, ncomp, sizeof(int), cudaMemcpyDeviceToHost, st));
     MGE_CUDA(ctx, cudaMemcpyAsync(&h_den, den_max, sizeof(double), cudaMemcpyDeviceToHost, st));
     MGE_CUDA(ctx, cudaMemcpyAsync(&h_nq, normq, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -665,6 +681,7 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
     if (h_err & ERR_LOOP) { set_error(ctx, "union-find iteration limit reached"); return MGE_ETIMEOUT; }
     ops->ncomp = h_ncomp;
     ops->norm_q = h_nq > 0 ? h_nq : 1.0;
+    ops->beta_q = h_bq > 0 ? h_bq : 2.0;
     // --- eps = lambda_2(Q) ---
     double eps = 0.0;
     if (o.eps_override_set) {
@@ -675,7 +692,8 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
       qop.val = (o.precision == MGE_FP64) ? (const void*)ops->q_val.p : (const void*)ops->q_val32.p;
       qop.shift = 0.0; qop.b = nullptr;
       qop.dinv = (o.precision == MGE_FP64) ? (const void*)ops->dinv_q.p : (const void*)ops->dinv_q32.p;
-      qop.norm = ops->norm_q; qop.bmax = 1.0; qop.deflate = true;
+      qop.norm = ops->norm_q; qop.bmax = 1.0; qop.deflate = true; qop.beta = ops->beta_q;
+      qop.precond_degree = o.eps_precond_degree > 0 ? std::min(o.eps_precond_degree, 64) : kDefaultPrecondDegree;
       int guard = o.eps_guard > 0 ? o.eps_guard : 3;
       int m = round_block_width(1 + guard);
       if (m > n - 1) m = -1;
@@ -704,17 +722,22 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
   }
 
   // --- A values, radii, B ---
-  MGE_TRY(ops->a_col.alloc(ctx, ops->nnz_a));
-  MGE_TRY(ops->a_val.alloc(ctx, ops->nnz_a));
-  MGE_TRY(ops->a_val32.alloc(ctx, ops->nnz_a));
+  MGE_TRY(ops->a_col.alloc(ctx, ops->nnz_a + 4));
+  MGE_TRY(ops->a_val.alloc(ctx, ops->nnz_a + 4));
+  MGE_TRY(ops->a_val32.alloc(ctx, ops->nnz_a + 4));
+  MGE_CUDA(ctx, cudaMemsetAsync(ops->a_col.p + ops->nnz_a, 0, 4 * sizeof(int32_t), st));
+  MGE_CUDA(ctx, cudaMemsetAsync(ops->a_val.p + ops->nnz_a, 0, 4 * sizeof(double), st));
+  MGE_CUDA(ctx, cudaMemsetAsync(ops->a_val32.p + ops->nnz_a, 0, 4 * sizeof(float), st));
   // b carries 4 zeroed elements past n: the LOBPCG Gram copies b in tiles whose byte
   // count is rounded up to a multiple of 16
   MGE_TRY(ops->b.alloc(ctx, n + 4));
   MGE_TRY(ops->b32.alloc(ctx, n + 4));
   MGE_CUDA(ctx, cudaMemsetAsync(ops->b.p + n, 0, 4 * sizeof(double), st));
   MGE_CUDA(ctx, cudaMemsetAsync(ops->b32.p + n, 0, 4 * sizeof(float), st));
-  MGE_TRY(ops->dinv_a.alloc(ctx, n));
-  MGE_TRY(ops->dinv_a32.alloc(ctx, n));
+  MGE_TRY(ops->dinv_a.alloc(ctx, n + 4));
+  MGE_CUDA(ctx, cudaMemsetAsync(ops->dinv_a.p + n, 0, 4 * sizeof(double), st));
+  MGE_TRY(ops->dinv_a32.alloc(ctx, n + 4));
+  MGE_CUDA(ctx, cudaMemsetAsync(ops->dinv_a32.p + n, 0, 4 * sizeof(float), st));
   DevBuf<double> r, logr;
   MGE_TRY(r.alloc(ctx, n));
   MGE_TRY(logr.alloc(ctx, n));
@@ -731,10 +754,11 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
     MGE_LAUNCHED(ctx, 2);
     k_finish_a<<<grid_for(n, B), B, 0, st>>>(n, ops->a_ptr.p, ops->a_col.p, ops->a_val.p, r.p, sumlog,
                                               ops->b.p, ops->b32.p, ops->dinv_a.p, ops->dinv_a32.p,
-                                              ops->a_val32.p, norma, bmax);
+                                              ops->a_val32.p, norma, bmax, beta_a);
     MGE_LAUNCHED(ctx, 1);
     MGE_CUDA(ctx, cudaGetLastError());
-    double h_na = 0, h_bm = 0;
+    double h_na = 0, h_bm = 0, h_ba = 0;
+    MGE_CUDA(ctx, cudaMemcpyAsync(&h_ba, beta_a, sizeof(double), cudaMemcpyDeviceToHost, st));
     MGE_CUDA(ctx, cudaMemcpyAsync(&h_err, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     MGE_CUDA(ctx, cudaMemcpyAsync(&h_na, norma, sizeof(double), cudaMemcpyDeviceToHost, st));
     MGE_CUDA(ctx, cudaMemcpyAsync(&h_bm, bmax, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -747,6 +771,7 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
     ops->build_ms = ms;
     ops->norm_a = h_na > 0 ? h_na : 1.0;
     ops->bmax = h_bm > 0 ? h_bm : 1.0;
+    ops->beta_a = h_ba > 0 ? h_ba : 2.0;
   }
   if (h_err & ERR_ISOLATED) {
     set_error(ctx, "isolated node: a Gershgorin radius r_i is zero, so B is singular");

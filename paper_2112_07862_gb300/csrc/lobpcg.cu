@@ -37,144 +37,386 @@ namespace {
 template <typename T>
 struct SpmmArgs {
   int64_t n;
-  const int64_t* ptr;
-  const int32_t* col;
-  const T* val;
+  const int64_t* ptr;        // n + 2 entries (one padding entry)
+  const int32_t* col;        // nnz + 4 entries (padding)
+  const T* val;              // nnz + 4 entries (padding)
   T shift;
   const T* Wr;
   const T* X; const T* AX; const T* P; const T* AP;   // NULL when absent
   const SmallT<T>* sm;                                 // L, M_x L, M_p L, c L (NULL: plain A*Wr)
   T* W; T* AW;
-  const State* st;
+  State* st;
+  int tiles_per_cta;
+  // one step of the Chebyshev preconditioner (cheb != 0; Wr is then the iterate x_k):
+  //   z = R - D^-1 A (sy x_k),  d' = c1 (sd d) + c2 z,  x_{k+1} = sy x_k + d'
+  // with R the Jacobi-scaled residual block (cr), d the previous correction (cd), D^-1 (cdinv)
+  int cheb;
+  const T* cr; const T* cd; const T* cdinv;
+  T* cd_out; T* cx_out;
+  T sy, sd, c1, c2;
 };
 
 // Lanes per row: G = M/4 column groups (4-wide vectors) times S, the split of the row's
-// nonzeros; S makes every row a team of 6 or 8 lanes so that short rows still keep several
-// gathers in flight per warp.
+// nonzeros; every row is a team of 12 or 16 lanes, two rows per warp.
 template <int M> struct SpmmShape {
   static constexpr int G = M / 4;
   static constexpr int S = (G == 1) ? 16 : (G == 2) ? 8 : (G <= 4) ? 4 : 2;
   static constexpr int TEAM = G * S;
   static constexpr int RPW = 32 / TEAM;
-  static constexpr int BATCH = 4;     // nonzeros per lane whose index loads precede their gathers
+  static constexpr int BATCH = 4;     // nonzeros per lane whose gathers are issued together
 };
 
+// One pipeline stage of the SpMM: a tile of R rows with its row pointers, column indices and
+// values (when they fit in CAP), and the rows of W_raw, X, AX, P, AP the rows need.  Byte
+// offsets; every segment starts on a 128-byte boundary.
 template <typename T, int M>
-__global__ void __launch_bounds__(kThreads) k_spmm_w(SpmmArgs<T> a) {
+struct SpmmTile {
+  static constexpr int R = 32;
+  static constexpr int CAP = 2048;
+  static constexpr int up(int x) { return (x + 127) / 128 * 128; }
+  static constexpr int PTR = 0;
+  static constexpr int COL = up((R + 2) * 8);
+  static constexpr int VAL = COL + up((CAP + 8) * 4);
+  static constexpr int ROWB = up(R * M * (int)sizeof(T));
+  static constexpr int WR = VAL + up((CAP + 8) * (int)sizeof(T));
+  static constexpr int XR = WR + ROWB, AXR = XR + ROWB, PR = AXR + ROWB, APR = PR + ROWB;
+  static constexpr int BYTES = APR + ROWB;
+};
+constexpr int kSpmmStages = 3;
+constexpr int kSpmmConsumers = kThreads;           // 8 consumer warps
+constexpr int kSpmmThreads = kThreads + 32;        // plus one producer warp
+
+struct SpmmMeta {
+  int64_t pb;      // first nonzero of the tile
+  int64_t c0;      // first column index copied (pb rounded down to 16 bytes)
+  int64_t v0;      // first value copied
+  int rows;
+  int staged;      // column indices and values are in the stage
+};
+
+// Y = A X with A = shift I + the difference-form Laplacian part (a_ij (x_j - x_i)), fused with
+// the projection and normalisation of W when a.sm is set.  Each CTA owns a contiguous range
+// of tiles; its producer warp streams them through a ring of shared-memory stages with 1-D
+// bulk copies (TMA) so that the row pointers, column indices, values and row blocks never sit
+// on a dependent load chain; the consumer warps wait only for the gathers of X rows.
+template <typename T, int M>
+__global__ void __launch_bounds__(kSpmmThreads) k_spmm_w(SpmmArgs<T> a) {
   if (a.st && a.st->done) return;
   using Sh = SpmmShape<M>;
-  constexpr int G = Sh::G, S = Sh::S, TEAM = Sh::TEAM, RPW = Sh::RPW;
-  constexpr int NW = kThreads / 32;
-  __shared__ T sMxL[M * M], sMpL[M * M], sL[M * M], scL[M];
-  __shared__ T sW[NW][RPW][M], sAW[NW][RPW][M];
+  using Tl = SpmmTile<T, M>;
+  constexpr int G = Sh::G, S = Sh::S, TEAM = Sh::TEAM, RPW = Sh::RPW, BT = Sh::BATCH;
+  constexpr int NW = kSpmmConsumers / 32;
+  constexpr int TEAMS = NW * RPW;
+  constexpr int ST = kSpmmStages;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* empty = full + ST;
+  SpmmMeta* meta = reinterpret_cast<SpmmMeta*>(smem_raw + 64);
+  unsigned char* stages = smem_raw + 256;
+  // blocks of at most 8 columns keep the epilogue's row vectors in registers (assembled by
+  // shuffles); wider blocks stage them in shared memory
+  constexpr bool REG = (G <= 2) && (TEAM >= 2 * M);
+  // epilogue matrices stored transposed (column c contiguous) with a padded column stride,
+  // so that the 16-byte loads of different columns fall in different banks
+  constexpr int CS = M + 4;
+  __shared__ __align__(16) T sMxLt[M * CS], sMpLt[M * CS], sLt[M * CS];
+  __shared__ T scL[M];
+  __shared__ __align__(16) T sW[REG ? 1 : NW][RPW][M], sAW[REG ? 1 : NW][RPW][M];
   const bool fused = a.sm != nullptr;
+  const bool hx = fused && a.X, hp = fused && a.P;
+  const bool cheb = !fused && a.cheb != 0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t ntiles = (a.n + Tl::R - 1) / Tl::R;
+  const int64_t t0 = (int64_t)blockIdx.x * a.tiles_per_cta;
+  const int my = (int)max((int64_t)0, min((int64_t)a.tiles_per_cta, ntiles - t0));
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], kSpmmConsumers); }
+    mbar_fence_init();
+  }
   if (fused) {
-    for (int t = threadIdx.x; t < M * M; t += kThreads) {
-      int r = t / M, c = t % M;
-      sMxL[t] = a.sm->MxL[r * MAXM + c];
-      sMpL[t] = a.sm->MpL[r * MAXM + c];
-      sL[t] = a.sm->Linv[r * MAXM + c];
+    for (int t = threadIdx.x; t < M * M; t += kSpmmThreads) {
+      const int r = t / M, c = t % M;
+      sMxLt[c * CS + r] = a.sm->MxL[r * MAXM + c];
+      sMpLt[c * CS + r] = a.sm->MpL[r * MAXM + c];
+      sLt[c * CS + r] = a.sm->Linv[r * MAXM + c];
     }
-    for (int t = threadIdx.x; t < M; t += kThreads) scL[t] = a.sm->cL[t];
+    for (int t = threadIdx.x; t < M; t += kSpmmThreads) scL[t] = a.sm->cL[t];
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+
+  if (wid == NW) {
+    // ---------------- producer warp (one thread) ----------------
+    if (lane == 0) {
+      int i = 0;
+      for (; i < my; ++i) {
+        const int s = i % ST;
+        if (i >= ST && !mbar_wait(&empty[s], (uint32_t)((i / ST) - 1) & 1u)) {
+          if (a.st) { a.st->err = MGE_ETIMEOUT; a.st->bad_stage = 6; a.st->done = DONE_ERROR; }
+          break;
+        }
+        const int64_t r0 = (t0 + i) * Tl::R;
+        const int rows = (int)min((int64_t)Tl::R, a.n - r0);
+        const int64_t pb = a.ptr[r0], pe = a.ptr[r0 + rows];
+        const bool staged = pe - pb <= Tl::CAP;
+        constexpr int VE = 16 / (int)sizeof(T);              // values per 16 bytes
+        const int64_t c0 = pb & ~(int64_t)3, c1 = (pe + 3) & ~(int64_t)3;
+        const int64_t v0 = pb & ~(int64_t)(VE - 1), v1 = (pe + VE - 1) & ~(int64_t)(VE - 1);
+        const uint32_t bp = (uint32_t)(((rows + 2) / 2) * 2 * 8);
+        const uint32_t bc = staged ? (uint32_t)((c1 - c0) * 4) : 0u;
+        const uint32_t bv = staged ? (uint32_t)((v1 - v0) * (int64_t)sizeof(T)) : 0u;
+        const uint32_t br = (uint32_t)rows * M * (uint32_t)sizeof(T);
+        const uint32_t bd = cheb ? (((uint32_t)rows * (uint32_t)sizeof(T) + 15u) & ~15u) : 0u;
+        const uint32_t total = bp + bc + bv + br * (1u + (hx ? 2u : 0u) + (hp ? 2u : 0u) + (cheb ? 2u : 0u)) + bd;
+        meta[s].pb = pb; meta[s].c0 = c0; meta[s].v0 = v0; meta[s].rows = rows; meta[s].staged = staged;
+        unsigned char* sb = stages + (size_t)s * Tl::BYTES;
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&full[s], total);
+        bulk_g2s(sb + Tl::PTR, a.ptr + r0, bp, &full[s]);
+        if (staged) {
+          bulk_g2s(sb + Tl::COL, a.col + c0, bc, &full[s]);
+          bulk_g2s(sb + Tl::VAL, a.val + v0, bv, &full[s]);
+        }
+        bulk_g2s(sb + Tl::WR, a.Wr + r0 * M, br, &full[s]);
+        if (hx) {
+          bulk_g2s(sb + Tl::XR, a.X + r0 * M, br, &full[s]);
+          bulk_g2s(sb + Tl::AXR, a.AX + r0 * M, br, &full[s]);
+        }
+        if (hp) {
+          bulk_g2s(sb + Tl::PR, a.P + r0 * M, br, &full[s]);
+          bulk_g2s(sb + Tl::APR, a.AP + r0 * M, br, &full[s]);
+        }
+        if (cheb) {
+          bulk_g2s(sb + Tl::XR, a.cr + r0 * M, br, &full[s]);
+          bulk_g2s(sb + Tl::AXR, a.cd + r0 * M, br, &full[s]);
+          bulk_g2s(sb + Tl::PR, a.cdinv + r0, bd, &full[s]);
+        }
+      }
+      // no copy may still be landing when the block's shared memory is released
+      for (int u = max(0, i - ST); u < i; ++u) mbar_wait(&full[u % ST], (uint32_t)(u / ST) & 1u);
+    }
+    return;
+  }
+
+  // ---------------- consumer warps ----------------
   const int team = lane / TEAM, tl = lane % TEAM;
   const int sub = tl / G, g = tl % G, c0 = g * 4;     // nonzero slice and column group
   const bool lane_ok = team < RPW;
-  for (int64_t base = ((int64_t)blockIdx.x * NW + wid) * RPW; base < a.n;
-       base += (int64_t)gridDim.x * NW * RPW) {
-    const int64_t row = base + team;
-    const bool valid = lane_ok && row < a.n;
-    T acc[4] = {0, 0, 0, 0}, wi[4] = {0, 0, 0, 0};
-    if (valid) {
-      ldg4(a.Wr + row * M + c0, wi);
-      const int64_t pe = a.ptr[row + 1];
-      constexpr int BT = Sh::BATCH;
-      // BATCH nonzeros per lane at a time: their index and value loads are all issued, then
-      // their gathers; an empty slot gathers the row itself with value 0
-      for (int64_t p0 = a.ptr[row] + sub; p0 < pe; p0 += (int64_t)BT * S) {
-        int32_t j[BT];
-        T v[BT];
+  for (int i = 0; i < my; ++i) {
+    const int s = i % ST;
+    if (!mbar_wait(&full[s], (uint32_t)(i / ST) & 1u)) {
+      if (a.st) { a.st->err = MGE_ETIMEOUT; a.st->bad_stage = 6; a.st->done = DONE_ERROR; }
+      break;
+    }
+    const unsigned char* sb = stages + (size_t)s * Tl::BYTES;
+    const int64_t* sptr = reinterpret_cast<const int64_t*>(sb + Tl::PTR);
+    const int32_t* scol = reinterpret_cast<const int32_t*>(sb + Tl::COL);
+    const T* sval = reinterpret_cast<const T*>(sb + Tl::VAL);
+    const T* sWr = reinterpret_cast<const T*>(sb + Tl::WR);
+    const int64_t mpb = meta[s].pb, mc0 = meta[s].c0, mv0 = meta[s].v0;
+    const int rows = meta[s].rows;
+    const bool staged = meta[s].staged != 0;
+    const int64_t r0 = (t0 + i) * Tl::R;
+    for (int pass = 0; pass < (Tl::R + TEAMS - 1) / TEAMS; ++pass) {
+      const int r = pass * TEAMS + wid * RPW + team;
+      const bool valid = lane_ok && r < rows;
+      const int64_t row = r0 + r;
+      T acc[4] = {0, 0, 0, 0}, wi[4] = {0, 0, 0, 0};
+      if (valid) {
+        ld4(sWr + r * M + c0, wi);
+        const int64_t pb = sptr[r];
+        const int len = (int)(sptr[r + 1] - pb);
+        const int32_t* cp = staged ? scol + (pb - mc0) : a.col + pb;
+        const T* vp = staged ? sval + (pb - mv0) : a.val + pb;
+        // BATCH nonzeros per lane at a time: their indices and values, then their gathers
+        for (int k0 = sub; k0 < len; k0 += BT * S) {
+          int32_t j[BT];
+          T v[BT];
 #pragma unroll
-        for (int b = 0; b < BT; ++b) {
-          const int64_t p = p0 + (int64_t)b * S;
-          const bool ok = p < pe;
-          j[b] = ok ? __ldg(a.col + p) : (int32_t)row;
-          v[b] = ok ? __ldg(a.val + p) : T(0);
+          for (int b = 0; b < BT; ++b) {
+            const int k = k0 + b * S;
+            j[b] = k < len ? cp[k] : -1;
+            v[b] = k < len ? vp[k] : T(0);
+          }
+          T w[BT][4];
+#pragma unroll
+          for (int b = 0; b < BT; ++b) {
+            if (j[b] >= 0) {
+              ldg4(a.Wr + (size_t)j[b] * M + c0, w[b]);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) w[b][q] = wi[q];
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < BT; ++b)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += v[b] * (w[b][q] - wi[q]);
         }
-        T w[BT][4];
-#pragma unroll
-        for (int b = 0; b < BT; ++b) ldg4(a.Wr + (int64_t)j[b] * M + c0, w[b]);
-#pragma unroll
-        for (int b = 0; b < BT; ++b)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[q] += v[b] * (w[b][q] - wi[q]);
       }
-    }
-    // combine the S nonzero slices: lanes of slice 0 end up with the row sums
+      const bool lead = valid && sub == 0;
+      if (!fused || !REG) {
+        // combine the S nonzero slices: lanes of slice 0 end up with the row sums
 #pragma unroll
-    for (int off = (S / 2) * G; off >= G && off > 0; off >>= 1) {
+        for (int off = (S / 2) * G; off >= G && off > 0; off >>= 1) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], off);
-    }
-    const bool lead = valid && sub == 0;
-    if (!fused) {
-      if (lead) {
-        T y[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) y[q] = a.shift * wi[q] + acc[q];
-        st4(a.AW + row * M + c0, y);
+          for (int q = 0; q < 4; ++q) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], off);
+        }
       }
-      continue;
-    }
-    // projection against X, P and the constant vector, then the normalisation, folded into
-    // one product per output (L, M_x L, M_p L, c L prepared by the small kernel):
-    //   W  = W_raw L - X (M_x L) - P (M_p L) - 1 (c L)
-    //   AW = (A W_raw) L - shift 1 (c L) - AX (M_x L) - AP (M_p L)
-    // the row's W_raw and A W_raw go to shared memory; lane tl of the team then computes
-    // outputs tl, tl + TEAM, ... (W column o for o < M, AW column o - M otherwise)
-    if (lead) {
+      if (!fused) {
+        if (lead) {
+          T y[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        sW[wid][team][c0 + q] = wi[q];
-        sAW[wid][team][c0 + q] = a.shift * wi[q] + acc[q];
-      }
-    }
-    __syncwarp();
-    if (valid) {
-      for (int o = tl; o < 2 * M; o += TEAM) {
-        const bool isw = o < M;
-        const int c = isw ? o : o - M;
-        const T* v = isw ? sW[wid][team] : sAW[wid][team];
-        T r = (isw ? T(-1) : -a.shift) * scL[c];
+          for (int q = 0; q < 4; ++q) y[q] = a.shift * wi[q] + acc[q];
+          if (cheb) {
+            T rr[4], dd[4], dn[4], xn[4];
+            ld4(reinterpret_cast<const T*>(sb + Tl::XR) + r * M + c0, rr);
+            ld4(reinterpret_cast<const T*>(sb + Tl::AXR) + r * M + c0, dd);
+            const T dv = reinterpret_cast<const T*>(sb + Tl::PR)[r];
 #pragma unroll
-        for (int l = 0; l < M; ++l) r += v[l] * sL[l * M + c];
-        if (a.X) {
-          const T* xr = (isw ? a.X : a.AX) + row * M;
-#pragma unroll
-          for (int l = 0; l < M; l += 4) {
-            T xv[4];
-            ldg4(xr + l, xv);
-#pragma unroll
-            for (int t = 0; t < 4; ++t) r -= xv[t] * sMxL[(l + t) * M + c];
+            for (int q = 0; q < 4; ++q) {
+              const T z = rr[q] - dv * (a.sy * y[q]);
+              dn[q] = a.c1 * (a.sd * dd[q]) + a.c2 * z;
+              xn[q] = a.sy * wi[q] + dn[q];
+            }
+            st4(a.cd_out + row * M + c0, dn);
+            st4(a.cx_out + row * M + c0, xn);
+          } else {
+            st4(a.AW + row * M + c0, y);
           }
         }
-        if (a.P) {
-          const T* pr = (isw ? a.P : a.AP) + row * M;
+        continue;
+      }
+      // projection against X, P and the constant vector, then the normalisation, folded
+      // into one product per output (L, M_x L, M_p L, c L prepared by the small kernel):
+      //   W  = W_raw L - X (M_x L) - P (M_p L) - 1 (c L)
+      //   AW = (A W_raw) L - shift 1 (c L) - AX (M_x L) - AP (M_p L)
+      // lane tl of the team computes outputs tl, tl + TEAM, ... (W column o for o < M, AW
+      // column o - M otherwise); the X, AX, P, AP rows come from the stage
+      const T* sX = reinterpret_cast<const T*>(sb + Tl::XR) + r * M;
+      const T* sAX = reinterpret_cast<const T*>(sb + Tl::AXR) + r * M;
+      const T* sP = reinterpret_cast<const T*>(sb + Tl::PR) + r * M;
+      const T* sAP = reinterpret_cast<const T*>(sb + Tl::APR) + r * M;
+      if constexpr (REG) {
+        // every lane gets its column group's row sums (butterfly over the slices), then the
+        // whole row of W_raw and of A W_raw from the lanes of the other group
 #pragma unroll
-          for (int l = 0; l < M; l += 4) {
-            T pv[4];
-            ldg4(pr + l, pv);
+        for (int off = (S / 2) * G; off >= G && off > 0; off >>= 1) {
 #pragma unroll
-            for (int t = 0; t < 4; ++t) r -= pv[t] * sMpL[(l + t) * M + c];
+          for (int q = 0; q < 4; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+        }
+        T wf[M], yf[M];
+#pragma unroll
+        for (int gg = 0; gg < G; ++gg) {
+          const int src = lane - g + gg;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const T wq = __shfl_sync(0xffffffffu, wi[q], src);
+            const T aq = __shfl_sync(0xffffffffu, acc[q], src);
+            wf[gg * 4 + q] = wq;
+            yf[gg * 4 + q] = a.shift * wq + aq;
           }
         }
-        (isw ? a.W : a.AW)[row * M + c] = r;
+        if (valid && tl < 2 * M) {
+          const bool isw = tl < M;
+          const int c = isw ? tl : tl - M;
+          T r0v = (isw ? T(-1) : -a.shift) * scL[c], r1v = T(0);
+#pragma unroll
+          for (int l = 0; l < M; l += 4) {
+            T lc[4];
+            ld4(sLt + c * CS + l, lc);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) r0v += (isw ? wf[l + t] : yf[l + t]) * lc[t];
+          }
+          if (hx) {
+            const T* xr = isw ? sX : sAX;
+#pragma unroll
+            for (int l = 0; l < M; l += 4) {
+              T xv[4], mc[4];
+              ld4(xr + l, xv);
+              ld4(sMxLt + c * CS + l, mc);
+#pragma unroll
+              for (int t = 0; t < 4; ++t) r1v -= xv[t] * mc[t];
+            }
+          }
+          if (hp) {
+            const T* pr = isw ? sP : sAP;
+#pragma unroll
+            for (int l = 0; l < M; l += 4) {
+              T pv[4], mc[4];
+              ld4(pr + l, pv);
+              ld4(sMpLt + c * CS + l, mc);
+#pragma unroll
+              for (int t = 0; t < 4; ++t) r1v -= pv[t] * mc[t];
+            }
+          }
+          (isw ? a.W : a.AW)[row * M + c] = r0v + r1v;
+        }
+      } else {
+        // the row's W_raw and A W_raw go to shared memory for the whole team
+        if (lead) {
+          T y[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) y[q] = a.shift * wi[q] + acc[q];
+          st4(&sW[wid][team][c0], wi);
+          st4(&sAW[wid][team][c0], y);
+        }
+        __syncwarp();
+        if (valid) {
+          for (int o = tl; o < 2 * M; o += TEAM) {
+            const bool isw = o < M;
+            const int c = isw ? o : o - M;
+            T r0v = (isw ? T(-1) : -a.shift) * scL[c], r1v = T(0);
+#pragma unroll
+            for (int l = 0; l < M; l += 4) {
+              T vv[4], lc[4];
+              if (isw) ld4(&sW[wid][team][l], vv);
+              else ld4(&sAW[wid][team][l], vv);
+              ld4(sLt + c * CS + l, lc);
+#pragma unroll
+              for (int t = 0; t < 4; ++t) r0v += vv[t] * lc[t];
+            }
+            if (hx) {
+              const T* xr = isw ? sX : sAX;
+#pragma unroll
+              for (int l = 0; l < M; l += 4) {
+                T xv[4], mc[4];
+                ld4(xr + l, xv);
+                ld4(sMxLt + c * CS + l, mc);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) r1v -= xv[t] * mc[t];
+              }
+            }
+            if (hp) {
+              const T* pr = isw ? sP : sAP;
+#pragma unroll
+              for (int l = 0; l < M; l += 4) {
+                T pv[4], mc[4];
+                ld4(pr + l, pv);
+                ld4(sMpLt + c * CS + l, mc);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) r1v -= pv[t] * mc[t];
+              }
+            }
+            (isw ? a.W : a.AW)[row * M + c] = r0v + r1v;
+          }
+        }
+        __syncwarp();
       }
     }
-    __syncwarp();
+    mbar_arrive(&empty[s]);      // this thread is done with stage s
   }
+}
+
+template <typename T, int M>
+size_t spmm_smem() { return 256 + (size_t)kSpmmStages * SpmmTile<T, M>::BYTES; }
+
+template <typename T, int M>
+int spmm_grid(const Ctx* ctx, int64_t n, int* tiles_per_cta) {
+  const int64_t ntiles = (n + SpmmTile<T, M>::R - 1) / SpmmTile<T, M>::R;
+  const int per_sm = std::max<int>(1, (int)((227 * 1024) / (spmm_smem<T, M>() + 1024)));
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * std::min(per_sm, 4)));
+  *tiles_per_cta = (int)((ntiles + grid - 1) / grid);
+  return (int)((ntiles + *tiles_per_cta - 1) / *tiles_per_cta);
 }
 
 // =======================================================================================
@@ -622,11 +864,17 @@ struct Solver {
   int K;
   int64_t n;
   DevBuf<T> X, AX, P, AP, W, AW, Wr;
+  // Chebyshev preconditioner: iterates x_k (two buffers), corrections d_k, and the block the
+  // W-side kernels read (W_raw itself at the start, the preconditioned block afterwards)
+  int cheb_deg = 1;
+  double ch_theta = 1, ch_delta = 1, ch_sigma = 1;
+  DevBuf<T> Yc0, Yc1, Dc;
+  const T* wsrc = nullptr;
   DevBuf<unsigned char> small;
   Small* sm = nullptr;
   SmallT<T>* smt = nullptr;
   State* state = nullptr;
-  int grid_rows = 0, grid_upd = 0, grid_gram = 0;
+  int grid_rows = 0, grid_upd = 0, grid_gram = 0, spmm_tpc = 1;
   double tol;
   int maxiter;
   bool inverse_rr = true;
@@ -648,6 +896,19 @@ struct Solver {
     MGE_TRY(P.alloc(ctx, blk)); MGE_TRY(AP.alloc(ctx, blk));
     MGE_TRY(W.alloc(ctx, blk)); MGE_TRY(AW.alloc(ctx, blk));
     MGE_TRY(Wr.alloc(ctx, blk));
+    wsrc = Wr.p;
+    cheb_deg = std::max(1, std::min(op.precond_degree, 64));
+    if (cheb_deg > 1) {
+      MGE_TRY(Yc0.alloc(ctx, blk)); MGE_TRY(Yc1.alloc(ctx, blk)); MGE_TRY(Dc.alloc(ctx, blk));
+      // Chebyshev iteration for A y = r on [alpha, beta] of the spectrum of D^-1 A: beta is the
+      // Gershgorin bound, alpha = beta / (2 d^2) so that the polynomial reduces the condition
+      // number of the preconditioned block by about d^2
+      const double beta = op.beta > 0 ? op.beta : 2.0;
+      const double alpha = beta * 0.5 / ((double)cheb_deg * cheb_deg);
+      ch_theta = 0.5 * (beta + alpha);
+      ch_delta = 0.5 * (beta - alpha);
+      ch_sigma = ch_theta / ch_delta;
+    }
     size_t off_t = ((sizeof(Small) + 255) / 256) * 256;
     size_t off_s = off_t + ((sizeof(SmallT<T>) + 255) / 256) * 256;
     size_t bytes = off_s + sizeof(State);
@@ -656,9 +917,7 @@ struct Solver {
     sm = reinterpret_cast<Small*>(small.p);
     smt = reinterpret_cast<SmallT<T>*>(small.p + off_t);
     state = reinterpret_cast<State*>(small.p + off_s);
-    const int spmm_rows_per_cta = SpmmShape<M>::RPW * (kThreads / 32);
-    int64_t sctas = (n + spmm_rows_per_cta - 1) / spmm_rows_per_cta;
-    grid_rows = (int)std::max<int64_t>(1, std::min<int64_t>(sctas, (int64_t)ctx->num_sms * 8));
+    grid_rows = spmm_grid<T, M>(ctx, n, &spmm_tpc);
     constexpr int RPW = 32 / (M / 4);
     const int rows_per_cta = RPW * (kThreads / 32);
     const int max_red = std::min(2 * ctx->num_sms, MAXCL * CL);
@@ -728,7 +987,7 @@ struct Solver {
     SpmmArgs<T> s{};
     s.n = n; s.ptr = op.ptr; s.col = op.col; s.val = static_cast<const T*>(op.val);
     s.shift = (T)op.shift;
-    s.Wr = Wr.p;
+    s.Wr = wsrc;
     s.X = hx ? X.p : nullptr; s.AX = hx ? AX.p : nullptr;
     s.P = hp ? P.p : nullptr; s.AP = hp ? AP.p : nullptr;
     s.sm = smt;
@@ -754,7 +1013,8 @@ struct Solver {
       if (cap == cudaStreamCaptureStatusActive) MGE_CUDA(ctx, cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal));
       else MGE_CUDA(ctx, cudaEventRecord(e0, st));
     }
-    k_spmm_w<T, M><<<grid_rows, kThreads, 0, st>>>(s);
+    s.tiles_per_cta = spmm_tpc;
+    k_spmm_w<T, M><<<grid_rows, kSpmmThreads, spmm_smem<T, M>(), st>>>(s);
     MGE_LAUNCHED(ctx, 1);
     if (timed) {
       if (cap == cudaStreamCaptureStatusActive) MGE_CUDA(ctx, cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal));
@@ -794,6 +1054,39 @@ struct Solver {
     MGE_LAUNCHED(ctx, 1);
   }
 
+  // W_raw <- p(D^-1 A) D^-1 R: cheb_deg - 1 steps of the Chebyshev iteration for A y = R with
+  // y_0 = 0 (Saad, Iterative Methods for Sparse Linear Systems, Alg. 12.1), each one SpMM
+  void launch_cheb() {
+    wsrc = Wr.p;
+    if (cheb_deg <= 1) return;
+    T* ys[2] = {Yc0.p, Yc1.p};
+    double rho_prev = 1.0 / ch_sigma;
+    for (int k = 1; k < cheb_deg; ++k) {
+      const double rho = 1.0 / (2.0 * ch_sigma - rho_prev);
+      SpmmArgs<T> s{};
+      s.n = n; s.ptr = op.ptr; s.col = op.col; s.val = static_cast<const T*>(op.val);
+      s.shift = (T)op.shift;
+      s.Wr = (k == 1) ? Wr.p : ys[k % 2];                 // x_k (x_1 = R / theta)
+      s.sm = nullptr; s.W = nullptr; s.AW = nullptr;
+      s.st = state;
+      s.tiles_per_cta = spmm_tpc;
+      s.cheb = 1;
+      s.cr = Wr.p;
+      s.cd = (k == 1) ? Wr.p : Dc.p;                      // d_0 = R / theta
+      s.cdinv = static_cast<const T*>(op.dinv);
+      s.cd_out = Dc.p;
+      s.cx_out = ys[(k + 1) % 2];
+      s.sy = (k == 1) ? (T)(1.0 / ch_theta) : T(1);
+      s.sd = (k == 1) ? (T)(1.0 / ch_theta) : T(1);
+      s.c1 = (T)(rho * rho_prev);
+      s.c2 = (T)(2.0 * rho / ch_delta);
+      k_spmm_w<T, M><<<grid_rows, kSpmmThreads, spmm_smem<T, M>(), st>>>(s);
+      MGE_LAUNCHED(ctx, 1);
+      rho_prev = rho;
+    }
+    wsrc = ys[cheb_deg % 2];
+  }
+
   void launch_wprep_(bool hx, bool hp, bool check) {
     WprepArgs w{};
     w.sm = sm; w.smt = smt; w.is_double = sizeof(T) == 8;
@@ -810,8 +1103,8 @@ struct Solver {
     int nl = 0;
     if (hx) L[nl++] = X.p;
     if (hp) L[nl++] = P.p;
-    L[nl++] = Wr.p;
-    const T* R2[1] = {Wr.p};
+    L[nl++] = wsrc;
+    const T* R2[1] = {wsrc};
     launch_gram(nl, L, 0, nullptr, 1, R2, false, op.b != nullptr, nullptr, &sm->partW[0][0], MAXM,
                 MAXS * MAXM, op.deflate);
   }
@@ -830,6 +1123,7 @@ struct Solver {
     launch_gram_s(nb);
     launch_rr_(nb, M);
     launch_update(nb, false, true);
+    launch_cheb();
     launch_gram_w(true, true);
     launch_wprep_(true, true, true);
     return MGE_OK;
@@ -845,12 +1139,14 @@ struct Solver {
     // --- init: W_raw = X0, normalise, Rayleigh-Ritz on span(W) ---
     k_init_block<T><<<gridn(n * M, 256), 256, 0, st>>>(n, M, seed, x0, x0_cols, Wr.p);
     MGE_LAUNCHED(ctx, 1);
+    wsrc = Wr.p;
     launch_gram_w(false, false);
     launch_wprep_(false, false, false);
     MGE_TRY(launch_spmm(false, false, timed));
     launch_gram_s(1);
     launch_rr_(1, 0);
     launch_update(1, true, false);
+    launch_cheb();
     launch_gram_w(true, false);
     launch_wprep_(true, false, true);
     // --- first iteration: S = [X W] ---
@@ -858,6 +1154,7 @@ struct Solver {
     launch_gram_s(2);
     launch_rr_(2, M);
     launch_update(2, false, true);
+    launch_cheb();
     launch_gram_w(true, true);
     launch_wprep_(true, true, true);
     MGE_CUDA(ctx, cudaGetLastError());
@@ -901,7 +1198,7 @@ struct Solver {
       MGE_CUDA(ctx, cudaGraphInstantiate(&gexec, graph, 0));
       if (timed) { ctx->ev_used = 0; ctx->ev_bytes.clear(); }
     }
-    const uint64_t per_chunk = (uint64_t)check_every * 6;
+    const uint64_t per_chunk = (uint64_t)check_every * (6 + (cheb_deg - 1));
     for (;;) {
       MGE_CUDA(ctx, cudaMemcpyAsync(hst, state, sizeof(State), cudaMemcpyDeviceToHost, st));
       MGE_CUDA(ctx, cudaStreamSynchronize(st));
@@ -975,6 +1272,8 @@ mge_status solve_m(Ctx* ctx, cudaStream_t st, const LobOp& op, int K, double tol
   MGE_CUDA(ctx, cudaStreamSynchronize(st));
   s.nnz_a = nnz;
   MGE_CUDA(ctx, cudaFuncSetAttribute(k_gram<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+  MGE_CUDA(ctx, cudaFuncSetAttribute(k_spmm_w<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)spmm_smem<T, M>()));
   MGE_CUDA(ctx, rr_configure());
   return s.run(check_every, use_graph, seed, x0, x0_cols, V_out, res);
 }
@@ -1001,10 +1300,10 @@ mge_status apply_m(Ctx* ctx, cudaStream_t st, const LobOp& op, const void* X, vo
   s.n = op.n; s.ptr = op.ptr; s.col = op.col; s.val = static_cast<const T*>(op.val);
   s.shift = (T)op.shift; s.Wr = static_cast<const T*>(X); s.AW = static_cast<T*>(Y);
   s.W = nullptr; s.sm = nullptr; s.st = nullptr;
-  const int rows_per_cta = SpmmShape<M>::RPW * (kThreads / 32);
-  int64_t ctas = (op.n + rows_per_cta - 1) / rows_per_cta;
-  int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, (int64_t)ctx->num_sms * 8));
-  k_spmm_w<T, M><<<grid, kThreads, 0, st>>>(s);
+  MGE_CUDA(ctx, cudaFuncSetAttribute(k_spmm_w<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)spmm_smem<T, M>()));
+  const int grid = spmm_grid<T, M>(ctx, op.n, &s.tiles_per_cta);
+  k_spmm_w<T, M><<<grid, kSpmmThreads, spmm_smem<T, M>(), st>>>(s);
   MGE_LAUNCHED(ctx, 1);
   MGE_CUDA(ctx, cudaGetLastError());
   return MGE_OK;

@@ -110,6 +110,7 @@ struct Ops {
   DevBuf<double>  b, dinv_a, dinv_q;         // B diagonal, Jacobi preconditioners
   DevBuf<float>   b32, dinv_a32, dinv_q32;
   double eps = 0, mu = 0, norm_a = 0, norm_q = 0, bmax = 1;
+  double beta_a = 2, beta_q = 2;            // Gershgorin bounds of the spectra of D^-1 A, D^-1 Q
   int degenerate = 0, ncomp = 1, eps_iters = 0;
   double eps_resid = 0, build_ms = 0;
 };
@@ -117,6 +118,9 @@ struct Ops {
 // ---------------------------------------------------------------------------------------
 // LOBPCG operator description handed to the solver
 // ---------------------------------------------------------------------------------------
+// default degree of the Chebyshev preconditioner of the LOBPCG solves
+constexpr int kDefaultPrecondDegree = 12;
+
 struct LobOp {
   int64_t n = 0;
   const int64_t* ptr = nullptr;
@@ -127,6 +131,8 @@ struct LobOp {
   const void* dinv = nullptr;      // Jacobi preconditioner diag(A)^-1
   double norm = 1, bmax = 1;       // ||A||_G and max b for the backward error
   bool deflate = false;            // keep blocks orthogonal to the constant vector
+  double beta = 2;                 // upper bound of the spectrum of diag(A)^-1 A
+  int precond_degree = 1;          // Chebyshev preconditioner degree (1: Jacobi)
 };
 
 struct LobResult {

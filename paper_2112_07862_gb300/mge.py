@@ -39,7 +39,7 @@ class mge_ops_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("eps_override_set", C.c_int), ("eps_override", C.c_double),
                 ("mu_override_set", C.c_int), ("mu_override", C.c_double), ("eps_tol", C.c_double),
                 ("eps_guard", C.c_int), ("eps_maxiter", C.c_int), ("seed", C.c_uint64),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("eps_precond_degree", C.c_int)]
 
 
 class mge_ops_info_t(C.Structure):
@@ -52,7 +52,8 @@ class mge_ops_info_t(C.Structure):
 class mge_embed_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("guard", C.c_int), ("maxiter", C.c_int), ("seed", C.c_uint64),
                 ("check_every", C.c_int), ("use_graph", C.c_int), ("x0", C.c_void_p), ("x0_cols", C.c_int),
-                ("x0_on_device", C.c_int), ("v_on_device", C.c_int), ("stream", C.c_void_p)]
+                ("x0_on_device", C.c_int), ("v_on_device", C.c_int), ("stream", C.c_void_p),
+                ("precond_degree", C.c_int)]
 
 
 class mge_embed_info(C.Structure):
@@ -254,7 +255,7 @@ def mge_release(ctx, ticket: int) -> int:
 # ---- conveniences ------------------------------------------------------------------------
 
 def ops_opts(precision="fp32", eps=None, mu=None, eps_tol=0.0, seed=0, stream=None, eps_guard=0,
-             eps_maxiter=0) -> mge_ops_opts:
+             eps_maxiter=0, eps_precond_degree=0) -> mge_ops_opts:
     o = mge_ops_opts()
     o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     if eps is not None:
@@ -266,11 +267,12 @@ def ops_opts(precision="fp32", eps=None, mu=None, eps_tol=0.0, seed=0, stream=No
     o.eps_maxiter = eps_maxiter
     o.seed = seed
     o.stream = stream
+    o.eps_precond_degree = eps_precond_degree
     return o
 
 
 def embed_opts(precision="fp32", guard=0, maxiter=0, seed=0, check_every=0, use_graph=True, x0=None,
-               v_on_device=False, stream=None) -> mge_embed_opts:
+               v_on_device=False, stream=None, precond_degree=0) -> mge_embed_opts:
     o = mge_embed_opts()
     o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     o.guard = guard
@@ -284,6 +286,7 @@ def embed_opts(precision="fp32", guard=0, maxiter=0, seed=0, check_every=0, use_
         o.x0_on_device = 1 if hasattr(x0, "data_ptr") else 0
     o.v_on_device = 1 if v_on_device else 0
     o.stream = stream
+    o.precond_degree = precond_degree
     return o
 
 
