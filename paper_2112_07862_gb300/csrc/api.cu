@@ -218,6 +218,15 @@ static LobOp make_op(const Ops& op, int which, int precision) {
     l.b = dbl ? (const void*)op.b.p : (const void*)op.b32.p;
     l.dinv = dbl ? (const void*)op.dinv_a.p : (const void*)op.dinv_a32.p;
     l.norm = op.norm_a; l.bmax = op.bmax; l.deflate = false; l.beta = op.beta_a;
+    // the preconditioner approximates A^-1 through L + eps I: mu Q moves only the bottom of
+    // the spectrum, by O(eps), and W has far fewer nonzeros than A
+    if (op.l_val.p) {
+      l.pc_ptr = op.w_ptr.p; l.pc_col = op.w_col.p;
+      l.pc_val = dbl ? (const void*)op.l_val.p : (const void*)op.l_val32.p;
+      l.pc_shift = op.eps;
+      l.pc_dinv = dbl ? (const void*)op.l_dinv.p : (const void*)op.l_dinv32.p;
+      l.pc_beta = op.beta_l;
+    }
   } else {
     l.ptr = op.q_ptr.p; l.col = op.q_col.p;
     l.val = dbl ? (const void*)op.q_val.p : (const void*)op.q_val32.p;

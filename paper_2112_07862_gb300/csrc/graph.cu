@@ -505,6 +505,26 @@ __global__ void k_finish_a(int64_t n, const int64_t* __restrict__ ap, const int3
   if (aii > 0) atomic_max_nonneg(beta_max, (aii + r[i]) * d);
 }
 
+// L + eps I for the preconditioner: values -w_ij (difference form, shift eps), its diagonal
+// scaling 1 / (d_i + eps) and the Gershgorin bound of the scaled spectrum
+__global__ void k_fill_proxy(int64_t n, const int64_t* __restrict__ rp, const double* __restrict__ w,
+                             double eps, double* __restrict__ lv, float* __restrict__ lv32,
+                             double* __restrict__ ldinv, float* __restrict__ ldinv32, double* beta_max) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double deg = 0.0;
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+    const double v = w[p];
+    deg += v;
+    lv[p] = -v;
+    lv32[p] = (float)(-v);
+  }
+  const double diag = deg + eps;
+  const double d = diag > 0 ? 1.0 / diag : 1.0;
+  ldinv[i] = d; ldinv32[i] = (float)d;
+  if (diag > 0) atomic_max_nonneg(beta_max, (diag + deg) * d);
+}
+
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
 }  // namespace
@@ -545,8 +565,10 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
   const int64_t nnz = ends[1];
   ops->nnz_w = nnz;
   if (n > 0x7ffffffe) { set_error(ctx, "n exceeds int32 column range"); return MGE_EINVAL; }
-  MGE_TRY(ops->w_ptr.alloc(ctx, n + 1));
-  MGE_TRY(ops->w_col.alloc(ctx, nnz));
+  MGE_TRY(ops->w_ptr.alloc(ctx, n + 2));
+  MGE_TRY(ops->w_col.alloc(ctx, nnz + 4));
+  MGE_CUDA(ctx, cudaMemsetAsync(ops->w_ptr.p + n + 1, 0, sizeof(int64_t), st));
+  MGE_CUDA(ctx, cudaMemsetAsync(ops->w_col.p + nnz, 0, 4 * sizeof(int32_t), st));
   MGE_TRY(ops->w_val.alloc(ctx, nnz));
   cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   MGE_CUDA(ctx, cudaMemcpyAsync(ops->w_ptr.p, rp_in, (n + 1) * sizeof(int64_t), kind, st));
@@ -772,6 +794,26 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
     ops->norm_a = h_na > 0 ? h_na : 1.0;
     ops->bmax = h_bm > 0 ? h_bm : 1.0;
     ops->beta_a = h_ba > 0 ? h_ba : 2.0;
+  }
+  {
+    const int64_t nnz_w = ops->nnz_w;
+    MGE_TRY(ops->l_val.alloc(ctx, nnz_w + 4));
+    MGE_TRY(ops->l_val32.alloc(ctx, nnz_w + 4));
+    MGE_TRY(ops->l_dinv.alloc(ctx, n + 4));
+    MGE_TRY(ops->l_dinv32.alloc(ctx, n + 4));
+    MGE_CUDA(ctx, cudaMemsetAsync(ops->l_val.p + nnz_w, 0, 4 * sizeof(double), st));
+    MGE_CUDA(ctx, cudaMemsetAsync(ops->l_val32.p + nnz_w, 0, 4 * sizeof(float), st));
+    MGE_CUDA(ctx, cudaMemsetAsync(ops->l_dinv.p + n, 0, 4 * sizeof(double), st));
+    MGE_CUDA(ctx, cudaMemsetAsync(ops->l_dinv32.p + n, 0, 4 * sizeof(float), st));
+    double* beta_l = d_sc.p + 7;
+    MGE_CUDA(ctx, cudaMemsetAsync(beta_l, 0, sizeof(double), st));
+    k_fill_proxy<<<grid_for(n, B), B, 0, st>>>(n, ops->w_ptr.p, ops->w_val.p, ops->eps, ops->l_val.p,
+                                                ops->l_val32.p, ops->l_dinv.p, ops->l_dinv32.p, beta_l);
+    MGE_LAUNCHED(ctx, 1);
+    double h_bl = 0;
+    MGE_CUDA(ctx, cudaMemcpyAsync(&h_bl, beta_l, sizeof(double), cudaMemcpyDeviceToHost, st));
+    MGE_CUDA(ctx, cudaStreamSynchronize(st));
+    ops->beta_l = h_bl > 0 ? h_bl : 2.0;
   }
   if (h_err & ERR_ISOLATED) {
     set_error(ctx, "isolated node: a Gershgorin radius r_i is zero, so B is singular");

@@ -903,7 +903,8 @@ struct Solver {
       // Chebyshev iteration for A y = r on [alpha, beta] of the spectrum of D^-1 A: beta is the
       // Gershgorin bound, alpha = beta / (2 d^2) so that the polynomial reduces the condition
       // number of the preconditioned block by about d^2
-      const double beta = op.beta > 0 ? op.beta : 2.0;
+      const double beta_in = op.pc_ptr ? op.pc_beta : op.beta;
+      const double beta = beta_in > 0 ? beta_in : 2.0;
       const double alpha = beta * 0.5 / ((double)cheb_deg * cheb_deg);
       ch_theta = 0.5 * (beta + alpha);
       ch_delta = 0.5 * (beta - alpha);
@@ -1044,7 +1045,8 @@ struct Solver {
     u.produce_p = produce_p;
     u.smt = smt;
     u.b = static_cast<const T*>(op.b);
-    u.dinv = static_cast<const T*>(op.dinv);
+    // the residual is scaled by the diagonal of the operator the preconditioner applies
+    u.dinv = static_cast<const T*>(op.pc_ptr ? op.pc_dinv : op.dinv);
     u.Wr = Wr.p;
     u.partN = &sm->partN[0][0];
     u.st = state;
@@ -1064,8 +1066,14 @@ struct Solver {
     for (int k = 1; k < cheb_deg; ++k) {
       const double rho = 1.0 / (2.0 * ch_sigma - rho_prev);
       SpmmArgs<T> s{};
-      s.n = n; s.ptr = op.ptr; s.col = op.col; s.val = static_cast<const T*>(op.val);
-      s.shift = (T)op.shift;
+      s.n = n;
+      if (op.pc_ptr) {
+        s.ptr = op.pc_ptr; s.col = op.pc_col; s.val = static_cast<const T*>(op.pc_val);
+        s.shift = (T)op.pc_shift;
+      } else {
+        s.ptr = op.ptr; s.col = op.col; s.val = static_cast<const T*>(op.val);
+        s.shift = (T)op.shift;
+      }
       s.Wr = (k == 1) ? Wr.p : ys[k % 2];                 // x_k (x_1 = R / theta)
       s.sm = nullptr; s.W = nullptr; s.AW = nullptr;
       s.st = state;
@@ -1073,7 +1081,7 @@ struct Solver {
       s.cheb = 1;
       s.cr = Wr.p;
       s.cd = (k == 1) ? Wr.p : Dc.p;                      // d_0 = R / theta
-      s.cdinv = static_cast<const T*>(op.dinv);
+      s.cdinv = static_cast<const T*>(op.pc_ptr ? op.pc_dinv : op.dinv);
       s.cd_out = Dc.p;
       s.cx_out = ys[(k + 1) % 2];
       s.sy = (k == 1) ? (T)(1.0 / ch_theta) : T(1);

@@ -109,6 +109,12 @@ struct Ops {
   DevBuf<float>   q_val32, a_val32;          // FP32 copies for the reduced-precision forms
   DevBuf<double>  b, dinv_a, dinv_q;         // B diagonal, Jacobi preconditioners
   DevBuf<float>   b32, dinv_a32, dinv_q32;
+  // L + eps I in the SpMM's difference form (off-diagonal values -w_ij on W's structure):
+  // the operator the LOBPCG preconditioner of A applies, with its Jacobi scaling and the
+  // Gershgorin bound of its scaled spectrum
+  DevBuf<double>  l_val, l_dinv;
+  DevBuf<float>   l_val32, l_dinv32;
+  double beta_l = 2;
   double eps = 0, mu = 0, norm_a = 0, norm_q = 0, bmax = 1;
   double beta_a = 2, beta_q = 2;            // Gershgorin bounds of the spectra of D^-1 A, D^-1 Q
   int degenerate = 0, ncomp = 1, eps_iters = 0;
@@ -133,6 +139,14 @@ struct LobOp {
   bool deflate = false;            // keep blocks orthogonal to the constant vector
   double beta = 2;                 // upper bound of the spectrum of diag(A)^-1 A
   int precond_degree = 1;          // Chebyshev preconditioner degree (1: Jacobi)
+  // operator the preconditioner applies, in the same difference form (pc_ptr NULL: the
+  // operator itself); its diagonal scaling and Gershgorin bound
+  const int64_t* pc_ptr = nullptr;
+  const int32_t* pc_col = nullptr;
+  const void* pc_val = nullptr;
+  double pc_shift = 0;
+  const void* pc_dinv = nullptr;
+  double pc_beta = 2;
 };
 
 struct LobResult {
