@@ -110,7 +110,7 @@ typedef struct {
   uint64_t seed;              /* seed of the eps solve's initial block                      */
   void*    stream;            /* cudaStream_t or NULL                                       */
   int      eps_precond_degree; /* Chebyshev preconditioner degree of the eps solve (see
-                                 mge_embed_opts.precond_degree; 0 = default 12)              */
+                                 mge_embed_opts.precond_degree; 0 = default 24)              */
 } mge_ops_opts;
 
 /* Builds the operators of Sec. 4 for the graph W (n nodes, CSR as described above; host
@@ -205,7 +205,7 @@ typedef struct {
                                  Gershgorin bound of D^-1 A.  d = 1 is the Jacobi
                                  preconditioner; each degree above 1 costs one SpMM per
                                  iteration and cuts the iteration count about in proportion.
-                                 The paper leaves the preconditioner open.  0 = default 12;
+                                 The paper leaves the preconditioner open.  0 = default 24;
                                  at most 64.                                                */
 } mge_embed_opts;
 

@@ -125,7 +125,7 @@ struct Ops {
 // LOBPCG operator description handed to the solver
 // ---------------------------------------------------------------------------------------
 // default degree of the Chebyshev preconditioner of the LOBPCG solves
-constexpr int kDefaultPrecondDegree = 12;
+constexpr int kDefaultPrecondDegree = 24;
 
 struct LobOp {
   int64_t n = 0;
