@@ -269,7 +269,10 @@ def run_ours(a, dist):
         hbm, peak_src = 6800.0, "of fallback"
     achieved = (st.spmm_bytes / (st.spmm_ms / 1e3) / 1e9) if st.spmm_ms > 0 else None
     traffic = spmm_traffic_per_launch()
-    roofline = {"kernel": "k_spmm_w (SpMM of A with the fused W projection/normalisation)",
+    # k_spmm_w runs in two modes: A W_raw with the fused projection/normalisation of W (once per
+    # iteration) and the Chebyshev preconditioner steps on L + eps I (degree - 1 per
+    # iteration); achieved = algorithmic bytes of all timed launches / their summed event time
+    roofline = {"kernel": "k_spmm_w (fused A*W_raw, and the Chebyshev preconditioner steps on L + eps I)",
                 "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": (achieved / hbm) if achieved else None, "peak_source": peak_src,
                 "traffic": traffic, "launches_timed": st.spmm_launches,

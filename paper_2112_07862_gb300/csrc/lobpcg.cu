@@ -58,9 +58,12 @@ struct SpmmArgs {
 
 // Lanes per row: G = M/4 column groups (4-wide vectors) times S, the split of the row's
 // nonzeros; every row is a team of 12 or 16 lanes, two rows per warp.
-template <int M> struct SpmmShape {
+// SHORT halves the split for operators whose rows hold at most about half a batch of
+// nonzeros (the preconditioner's L + eps I on k-NN graphs), doubling the rows per warp.
+template <int M, bool SHORT = false> struct SpmmShape {
   static constexpr int G = M / 4;
-  static constexpr int S = (G == 1) ? 16 : (G == 2) ? 8 : (G <= 4) ? 4 : 2;
+  static constexpr int SL = (G == 1) ? 16 : (G == 2) ? 8 : (G <= 4) ? 4 : 2;
+  static constexpr int S = SHORT ? (SL > 1 ? SL / 2 : 1) : SL;
   static constexpr int TEAM = G * S;
   static constexpr int RPW = 32 / TEAM;
   static constexpr int BATCH = 4;     // nonzeros per lane whose gathers are issued together
@@ -99,10 +102,10 @@ struct SpmmMeta {
 // of tiles; its producer warp streams them through a ring of shared-memory stages with 1-D
 // bulk copies (TMA) so that the row pointers, column indices, values and row blocks never sit
 // on a dependent load chain; the consumer warps wait only for the gathers of X rows.
-template <typename T, int M>
+template <typename T, int M, bool SHORT>
 __global__ void __launch_bounds__(kSpmmThreads) k_spmm_w(SpmmArgs<T> a) {
   if (a.st && a.st->done) return;
-  using Sh = SpmmShape<M>;
+  using Sh = SpmmShape<M, SHORT>;
   using Tl = SpmmTile<T, M>;
   constexpr int G = Sh::G, S = Sh::S, TEAM = Sh::TEAM, RPW = Sh::RPW, BT = Sh::BATCH;
   constexpr int NW = kSpmmConsumers / 32;
@@ -409,6 +412,27 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm_w(SpmmArgs<T> a) {
 
 template <typename T, int M>
 size_t spmm_smem() { return 256 + (size_t)kSpmmStages * SpmmTile<T, M>::BYTES; }
+
+// rows short enough for the halved split: at most half a batch of nonzeros on average
+template <int M>
+bool spmm_short(int64_t nnz, int64_t n) {
+  return n > 0 && 2 * nnz <= (int64_t)SpmmShape<M>::SL * SpmmShape<M>::BATCH * n;
+}
+
+template <typename T, int M>
+void spmm_launch(int grid, cudaStream_t st, const SpmmArgs<T>& s, bool short_rows) {
+  if (short_rows) k_spmm_w<T, M, true><<<grid, kSpmmThreads, spmm_smem<T, M>(), st>>>(s);
+  else k_spmm_w<T, M, false><<<grid, kSpmmThreads, spmm_smem<T, M>(), st>>>(s);
+}
+
+template <typename T, int M>
+cudaError_t spmm_configure() {
+  cudaError_t e = cudaFuncSetAttribute(k_spmm_w<T, M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)spmm_smem<T, M>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_spmm_w<T, M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)spmm_smem<T, M>());
+}
 
 template <typename T, int M>
 int spmm_grid(const Ctx* ctx, int64_t n, int* tiles_per_cta) {
@@ -870,6 +894,7 @@ struct Solver {
   double ch_theta = 1, ch_delta = 1, ch_sigma = 1;
   DevBuf<T> Yc0, Yc1, Dc;
   const T* wsrc = nullptr;
+  std::vector<uint64_t> cap_bytes;     // bytes of the SpMM launches timed inside the graph
   DevBuf<unsigned char> small;
   Small* sm = nullptr;
   SmallT<T>* smt = nullptr;
@@ -879,7 +904,7 @@ struct Solver {
   int maxiter;
   bool inverse_rr = true;
   double tau = 1e-12, tau_p = 1e-16, tau_w = 1e-10;
-  int64_t nnz_a = 0;
+  int64_t nnz_a = 0, nnz_pc = 0;
 
   Solver(Ctx* c, cudaStream_t s, const LobOp& o, int k) : ctx(c), st(s), op(o), K(k), n(o.n) {}
 
@@ -984,6 +1009,42 @@ struct Solver {
     return b;
   }
 
+  // algorithmic bytes of one Chebyshev step: the operator's indices, values and row
+  // pointers, the gathered iterate once, R, d and D^-1 read, d and the next iterate written
+  uint64_t cheb_bytes() const {
+    uint64_t blk = (uint64_t)n * M * sizeof(T);
+    return (uint64_t)nnz_pc * (4 + sizeof(T)) + (uint64_t)(n + 1) * 8 + blk + 2 * blk +
+           (uint64_t)n * sizeof(T) + 2 * blk;
+  }
+
+  // CUDA-event timing of the SpMM launches (ctx->timing): inside a stream capture the
+  // records become external event nodes of the graph
+  cudaEvent_t tev1 = nullptr;
+  bool tcap = false;
+  mge_status time_begin(uint64_t bytes) {
+    if (ctx->ev_used >= ctx->ev_pool.size()) {
+      cudaEvent_t x, y;
+      MGE_CUDA(ctx, cudaEventCreate(&x));
+      MGE_CUDA(ctx, cudaEventCreate(&y));
+      ctx->ev_pool.push_back({x, y});
+    }
+    cudaEvent_t e0 = ctx->ev_pool[ctx->ev_used].first;
+    tev1 = ctx->ev_pool[ctx->ev_used].second;
+    ctx->ev_used++;
+    ctx->ev_bytes.push_back(bytes);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    MGE_CUDA(ctx, cudaStreamIsCapturing(st, &cap));
+    tcap = cap == cudaStreamCaptureStatusActive;
+    if (tcap) MGE_CUDA(ctx, cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal));
+    else MGE_CUDA(ctx, cudaEventRecord(e0, st));
+    return MGE_OK;
+  }
+  mge_status time_end() {
+    if (tcap) MGE_CUDA(ctx, cudaEventRecordWithFlags(tev1, st, cudaEventRecordExternal));
+    else MGE_CUDA(ctx, cudaEventRecord(tev1, st));
+    return MGE_OK;
+  }
+
   mge_status launch_spmm(bool hx, bool hp, bool timed) {
     SpmmArgs<T> s{};
     s.n = n; s.ptr = op.ptr; s.col = op.col; s.val = static_cast<const T*>(op.val);
@@ -994,33 +1055,11 @@ struct Solver {
     s.sm = smt;
     s.W = W.p; s.AW = AW.p;
     s.st = state;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (timed) {
-      if (ctx->ev_used >= ctx->ev_pool.size()) {
-        cudaEvent_t x, y;
-        MGE_CUDA(ctx, cudaEventCreate(&x));
-        MGE_CUDA(ctx, cudaEventCreate(&y));
-        ctx->ev_pool.push_back({x, y});
-      }
-      e0 = ctx->ev_pool[ctx->ev_used].first;
-      e1 = ctx->ev_pool[ctx->ev_used].second;
-      ctx->ev_used++;
-      ctx->ev_bytes.push_back(spmm_bytes(hx, hp));
-    }
-    // inside a stream capture the records become external event nodes of the graph
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (timed) {
-      MGE_CUDA(ctx, cudaStreamIsCapturing(st, &cap));
-      if (cap == cudaStreamCaptureStatusActive) MGE_CUDA(ctx, cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal));
-      else MGE_CUDA(ctx, cudaEventRecord(e0, st));
-    }
     s.tiles_per_cta = spmm_tpc;
-    k_spmm_w<T, M><<<grid_rows, kSpmmThreads, spmm_smem<T, M>(), st>>>(s);
+    if (timed) MGE_TRY(time_begin(spmm_bytes(hx, hp)));
+    spmm_launch<T, M>(grid_rows, st, s, spmm_short<M>(nnz_a, n));
     MGE_LAUNCHED(ctx, 1);
-    if (timed) {
-      if (cap == cudaStreamCaptureStatusActive) MGE_CUDA(ctx, cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal));
-      else MGE_CUDA(ctx, cudaEventRecord(e1, st));
-    }
+    if (timed) MGE_TRY(time_end());
     return MGE_OK;
   }
 
@@ -1058,9 +1097,9 @@ struct Solver {
 
   // W_raw <- p(D^-1 A) D^-1 R: cheb_deg - 1 steps of the Chebyshev iteration for A y = R with
   // y_0 = 0 (Saad, Iterative Methods for Sparse Linear Systems, Alg. 12.1), each one SpMM
-  void launch_cheb() {
+  mge_status launch_cheb(bool timed) {
     wsrc = Wr.p;
-    if (cheb_deg <= 1) return;
+    if (cheb_deg <= 1) return MGE_OK;
     T* ys[2] = {Yc0.p, Yc1.p};
     double rho_prev = 1.0 / ch_sigma;
     for (int k = 1; k < cheb_deg; ++k) {
@@ -1088,11 +1127,14 @@ struct Solver {
       s.sd = (k == 1) ? (T)(1.0 / ch_theta) : T(1);
       s.c1 = (T)(rho * rho_prev);
       s.c2 = (T)(2.0 * rho / ch_delta);
-      k_spmm_w<T, M><<<grid_rows, kSpmmThreads, spmm_smem<T, M>(), st>>>(s);
+      if (timed) MGE_TRY(time_begin(cheb_bytes()));
+      spmm_launch<T, M>(grid_rows, st, s, spmm_short<M>(nnz_pc, n));
       MGE_LAUNCHED(ctx, 1);
+      if (timed) MGE_TRY(time_end());
       rho_prev = rho;
     }
     wsrc = ys[cheb_deg % 2];
+    return MGE_OK;
   }
 
   void launch_wprep_(bool hx, bool hp, bool check) {
@@ -1131,7 +1173,7 @@ struct Solver {
     launch_gram_s(nb);
     launch_rr_(nb, M);
     launch_update(nb, false, true);
-    launch_cheb();
+    MGE_TRY(launch_cheb(timed));
     launch_gram_w(true, true);
     launch_wprep_(true, true, true);
     return MGE_OK;
@@ -1154,7 +1196,7 @@ struct Solver {
     launch_gram_s(1);
     launch_rr_(1, 0);
     launch_update(1, true, false);
-    launch_cheb();
+    MGE_TRY(launch_cheb(timed));
     launch_gram_w(true, false);
     launch_wprep_(true, false, true);
     // --- first iteration: S = [X W] ---
@@ -1162,7 +1204,7 @@ struct Solver {
     launch_gram_s(2);
     launch_rr_(2, M);
     launch_update(2, false, true);
-    launch_cheb();
+    MGE_TRY(launch_cheb(timed));
     launch_gram_w(true, true);
     launch_wprep_(true, true, true);
     MGE_CUDA(ctx, cudaGetLastError());
@@ -1204,7 +1246,7 @@ struct Solver {
       if (ce != cudaSuccess) { set_error(ctx, "graph capture failed: %s", cudaGetErrorString(ce)); return MGE_EDEVICE; }
       ctx->kernel_launches = before;
       MGE_CUDA(ctx, cudaGraphInstantiate(&gexec, graph, 0));
-      if (timed) { ctx->ev_used = 0; ctx->ev_bytes.clear(); }
+      if (timed) { cap_bytes = ctx->ev_bytes; ctx->ev_used = 0; ctx->ev_bytes.clear(); }
     }
     const uint64_t per_chunk = (uint64_t)check_every * (6 + (cheb_deg - 1));
     for (;;) {
@@ -1213,8 +1255,9 @@ struct Solver {
       if (hst->done != DONE_RUNNING) break;
       if (graph_ok) {
         if (timed) {
-          ctx->ev_used = 1;
-          ctx->ev_bytes.assign(1, spmm_bytes(true, true));
+          // the events recorded in the first captured iteration fire on every launch
+          ctx->ev_used = cap_bytes.size();
+          ctx->ev_bytes = cap_bytes;
         }
         MGE_CUDA(ctx, cudaGraphLaunch(gexec, st));
         ctx->kernel_launches += per_chunk;
@@ -1279,9 +1322,13 @@ mge_status solve_m(Ctx* ctx, cudaStream_t st, const LobOp& op, int K, double tol
   MGE_CUDA(ctx, cudaMemcpyAsync(&nnz, op.ptr + op.n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   MGE_CUDA(ctx, cudaStreamSynchronize(st));
   s.nnz_a = nnz;
+  s.nnz_pc = nnz;
+  if (op.pc_ptr) {
+    MGE_CUDA(ctx, cudaMemcpyAsync(&s.nnz_pc, op.pc_ptr + op.n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  }
   MGE_CUDA(ctx, cudaFuncSetAttribute(k_gram<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-  MGE_CUDA(ctx, cudaFuncSetAttribute(k_spmm_w<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)spmm_smem<T, M>()));
+  MGE_CUDA(ctx, (spmm_configure<T, M>()));
   MGE_CUDA(ctx, rr_configure());
   return s.run(check_every, use_graph, seed, x0, x0_cols, V_out, res);
 }
@@ -1308,10 +1355,12 @@ mge_status apply_m(Ctx* ctx, cudaStream_t st, const LobOp& op, const void* X, vo
   s.n = op.n; s.ptr = op.ptr; s.col = op.col; s.val = static_cast<const T*>(op.val);
   s.shift = (T)op.shift; s.Wr = static_cast<const T*>(X); s.AW = static_cast<T*>(Y);
   s.W = nullptr; s.sm = nullptr; s.st = nullptr;
-  MGE_CUDA(ctx, cudaFuncSetAttribute(k_spmm_w<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)spmm_smem<T, M>()));
+  MGE_CUDA(ctx, (spmm_configure<T, M>()));
   const int grid = spmm_grid<T, M>(ctx, op.n, &s.tiles_per_cta);
-  k_spmm_w<T, M><<<grid, kSpmmThreads, spmm_smem<T, M>(), st>>>(s);
+  int64_t nnz = 0;
+  MGE_CUDA(ctx, cudaMemcpyAsync(&nnz, op.ptr + op.n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  spmm_launch<T, M>(grid, st, s, spmm_short<M>(nnz, op.n));
   MGE_LAUNCHED(ctx, 1);
   MGE_CUDA(ctx, cudaGetLastError());
   return MGE_OK;
