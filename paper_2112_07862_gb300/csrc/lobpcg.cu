@@ -72,10 +72,10 @@ template <int M, bool SHORT = false> struct SpmmShape {
 // One pipeline stage of the SpMM: a tile of R rows with its row pointers, column indices and
 // values (when they fit in CAP), and the rows of W_raw, X, AX, P, AP the rows need.  Byte
 // offsets; every segment starts on a 128-byte boundary.
-template <typename T, int M>
+template <typename T, int M, bool SHORT = false>
 struct SpmmTile {
   static constexpr int R = 32;
-  static constexpr int CAP = 2048;
+  static constexpr int CAP = SHORT ? 1024 : 2048;    // short rows: smaller stages, more CTAs/SM
   static constexpr int up(int x) { return (x + 127) / 128 * 128; }
   static constexpr int PTR = 0;
   static constexpr int COL = up((R + 2) * 8);
@@ -106,7 +106,7 @@ template <typename T, int M, bool SHORT>
 __global__ void __launch_bounds__(kSpmmThreads) k_spmm_w(SpmmArgs<T> a) {
   if (a.st && a.st->done) return;
   using Sh = SpmmShape<M, SHORT>;
-  using Tl = SpmmTile<T, M>;
+  using Tl = SpmmTile<T, M, SHORT>;
   constexpr int G = Sh::G, S = Sh::S, TEAM = Sh::TEAM, RPW = Sh::RPW, BT = Sh::BATCH;
   constexpr int NW = kSpmmConsumers / 32;
   constexpr int TEAMS = NW * RPW;
@@ -410,8 +410,8 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm_w(SpmmArgs<T> a) {
   }
 }
 
-template <typename T, int M>
-size_t spmm_smem() { return 256 + (size_t)kSpmmStages * SpmmTile<T, M>::BYTES; }
+template <typename T, int M, bool SHORT>
+size_t spmm_smem() { return 256 + (size_t)kSpmmStages * SpmmTile<T, M, SHORT>::BYTES; }
 
 // rows short enough for the halved split: at most half a batch of nonzeros on average
 template <int M>
@@ -419,29 +419,44 @@ bool spmm_short(int64_t nnz, int64_t n) {
   return n > 0 && 2 * nnz <= (int64_t)SpmmShape<M>::SL * SpmmShape<M>::BATCH * n;
 }
 
+// grid: as many CTAs as fit on the GPU at once (by shared memory), each owning a
+// contiguous range of tiles
+template <typename T, int M, bool SHORT>
+int spmm_grid(const Ctx* ctx, int64_t n, int* tiles_per_cta) {
+  static int per_sm = 0;                 // resident CTAs per SM (registers, shared memory)
+  if (per_sm == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmm_w<T, M, SHORT>, kSpmmThreads,
+                                                      spmm_smem<T, M, SHORT>()) != cudaSuccess || b < 1)
+      b = 1;
+    per_sm = b;
+  }
+  const int64_t ntiles = (n + SpmmTile<T, M, SHORT>::R - 1) / SpmmTile<T, M, SHORT>::R;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * per_sm));
+  *tiles_per_cta = (int)((ntiles + grid - 1) / grid);
+  return (int)((ntiles + *tiles_per_cta - 1) / *tiles_per_cta);
+}
+
 template <typename T, int M>
-void spmm_launch(int grid, cudaStream_t st, const SpmmArgs<T>& s, bool short_rows) {
-  if (short_rows) k_spmm_w<T, M, true><<<grid, kSpmmThreads, spmm_smem<T, M>(), st>>>(s);
-  else k_spmm_w<T, M, false><<<grid, kSpmmThreads, spmm_smem<T, M>(), st>>>(s);
+void spmm_launch(const Ctx* ctx, cudaStream_t st, SpmmArgs<T> s, bool short_rows) {
+  if (short_rows) {
+    const int grid = spmm_grid<T, M, true>(ctx, s.n, &s.tiles_per_cta);
+    k_spmm_w<T, M, true><<<grid, kSpmmThreads, spmm_smem<T, M, true>(), st>>>(s);
+  } else {
+    const int grid = spmm_grid<T, M, false>(ctx, s.n, &s.tiles_per_cta);
+    k_spmm_w<T, M, false><<<grid, kSpmmThreads, spmm_smem<T, M, false>(), st>>>(s);
+  }
 }
 
 template <typename T, int M>
 cudaError_t spmm_configure() {
   cudaError_t e = cudaFuncSetAttribute(k_spmm_w<T, M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)spmm_smem<T, M>());
+                                       (int)spmm_smem<T, M, false>());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_spmm_w<T, M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)spmm_smem<T, M>());
+                              (int)spmm_smem<T, M, true>());
 }
 
-template <typename T, int M>
-int spmm_grid(const Ctx* ctx, int64_t n, int* tiles_per_cta) {
-  const int64_t ntiles = (n + SpmmTile<T, M>::R - 1) / SpmmTile<T, M>::R;
-  const int per_sm = std::max<int>(1, (int)((227 * 1024) / (spmm_smem<T, M>() + 1024)));
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * std::min(per_sm, 4)));
-  *tiles_per_cta = (int)((ntiles + grid - 1) / grid);
-  return (int)((ntiles + *tiles_per_cta - 1) / *tiles_per_cta);
-}
 
 // =======================================================================================
 // Gram products over row tiles: out1 = L^T R1, out2 = L^T diag(b) R2 (block-upper part of
@@ -899,7 +914,7 @@ struct Solver {
   Small* sm = nullptr;
   SmallT<T>* smt = nullptr;
   State* state = nullptr;
-  int grid_rows = 0, grid_upd = 0, grid_gram = 0, spmm_tpc = 1;
+  int grid_upd = 0, grid_gram = 0;
   double tol;
   int maxiter;
   bool inverse_rr = true;
@@ -943,7 +958,6 @@ struct Solver {
     sm = reinterpret_cast<Small*>(small.p);
     smt = reinterpret_cast<SmallT<T>*>(small.p + off_t);
     state = reinterpret_cast<State*>(small.p + off_s);
-    grid_rows = spmm_grid<T, M>(ctx, n, &spmm_tpc);
     constexpr int RPW = 32 / (M / 4);
     const int rows_per_cta = RPW * (kThreads / 32);
     const int max_red = std::min(2 * ctx->num_sms, MAXCL * CL);
@@ -1055,9 +1069,8 @@ struct Solver {
     s.sm = smt;
     s.W = W.p; s.AW = AW.p;
     s.st = state;
-    s.tiles_per_cta = spmm_tpc;
     if (timed) MGE_TRY(time_begin(spmm_bytes(hx, hp)));
-    spmm_launch<T, M>(grid_rows, st, s, spmm_short<M>(nnz_a, n));
+    spmm_launch<T, M>(ctx, st, s, spmm_short<M>(nnz_a, n));
     MGE_LAUNCHED(ctx, 1);
     if (timed) MGE_TRY(time_end());
     return MGE_OK;
@@ -1116,8 +1129,7 @@ struct Solver {
       s.Wr = (k == 1) ? Wr.p : ys[k % 2];                 // x_k (x_1 = R / theta)
       s.sm = nullptr; s.W = nullptr; s.AW = nullptr;
       s.st = state;
-      s.tiles_per_cta = spmm_tpc;
-      s.cheb = 1;
+        s.cheb = 1;
       s.cr = Wr.p;
       s.cd = (k == 1) ? Wr.p : Dc.p;                      // d_0 = R / theta
       s.cdinv = static_cast<const T*>(op.pc_ptr ? op.pc_dinv : op.dinv);
@@ -1128,7 +1140,7 @@ struct Solver {
       s.c1 = (T)(rho * rho_prev);
       s.c2 = (T)(2.0 * rho / ch_delta);
       if (timed) MGE_TRY(time_begin(cheb_bytes()));
-      spmm_launch<T, M>(grid_rows, st, s, spmm_short<M>(nnz_pc, n));
+      spmm_launch<T, M>(ctx, st, s, spmm_short<M>(nnz_pc, n));
       MGE_LAUNCHED(ctx, 1);
       if (timed) MGE_TRY(time_end());
       rho_prev = rho;
@@ -1356,11 +1368,10 @@ mge_status apply_m(Ctx* ctx, cudaStream_t st, const LobOp& op, const void* X, vo
   s.shift = (T)op.shift; s.Wr = static_cast<const T*>(X); s.AW = static_cast<T*>(Y);
   s.W = nullptr; s.sm = nullptr; s.st = nullptr;
   MGE_CUDA(ctx, (spmm_configure<T, M>()));
-  const int grid = spmm_grid<T, M>(ctx, op.n, &s.tiles_per_cta);
   int64_t nnz = 0;
   MGE_CUDA(ctx, cudaMemcpyAsync(&nnz, op.ptr + op.n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   MGE_CUDA(ctx, cudaStreamSynchronize(st));
-  spmm_launch<T, M>(grid, st, s, spmm_short<M>(nnz, op.n));
+  spmm_launch<T, M>(ctx, st, s, spmm_short<M>(nnz, op.n));
   MGE_LAUNCHED(ctx, 1);
   MGE_CUDA(ctx, cudaGetLastError());
   return MGE_OK;
