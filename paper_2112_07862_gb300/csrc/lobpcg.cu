@@ -58,12 +58,13 @@ struct SpmmArgs {
 
 // Lanes per row: G = M/4 column groups (4-wide vectors) times S, the split of the row's
 // nonzeros; every row is a team of 12 or 16 lanes, two rows per warp.
-// SHORT halves the split for operators whose rows hold at most about half a batch of
-// nonzeros (the preconditioner's L + eps I on k-NN graphs), doubling the rows per warp.
+// SHORT is for operators whose rows hold at most about half a batch of nonzeros (the
+// preconditioner's L + eps I, and Q, on k-NN graphs): two lanes per row at m <= 8, each lane
+// walking the row's nonzeros itself (no split, no reduction), 16 rows per warp.
 template <int M, bool SHORT = false> struct SpmmShape {
   static constexpr int G = M / 4;
   static constexpr int SL = (G == 1) ? 16 : (G == 2) ? 8 : (G <= 4) ? 4 : 2;
-  static constexpr int S = SHORT ? (SL > 1 ? SL / 2 : 1) : SL;
+  static constexpr int S = !SHORT ? SL : (G == 1) ? 4 : (G == 2) ? 1 : (SL > 1 ? SL / 2 : 1);
   static constexpr int TEAM = G * S;
   static constexpr int RPW = 32 / TEAM;
   static constexpr int BATCH = 4;     // nonzeros per lane whose gathers are issued together
@@ -74,8 +75,11 @@ template <int M, bool SHORT = false> struct SpmmShape {
 // offsets; every segment starts on a 128-byte boundary.
 template <typename T, int M, bool SHORT = false>
 struct SpmmTile {
-  static constexpr int R = 32;
-  static constexpr int CAP = SHORT ? 1024 : 2048;    // short rows: smaller stages, more CTAs/SM
+  // one pass of the 8 consumer warps covers R rows (32, or the number of row teams)
+  static constexpr int TEAMS = SpmmShape<M, SHORT>::RPW * 8;
+  static constexpr int R = TEAMS <= 32 ? 32 : TEAMS;
+  static constexpr int CAP = (R > 32 || !SHORT) ? 2048 : 1024;
+  static constexpr int ST = (R >= 128) ? 2 : 3;      // pipeline stages
   static constexpr int up(int x) { return (x + 127) / 128 * 128; }
   static constexpr int PTR = 0;
   static constexpr int COL = up((R + 2) * 8);
@@ -85,7 +89,6 @@ struct SpmmTile {
   static constexpr int XR = WR + ROWB, AXR = XR + ROWB, PR = AXR + ROWB, APR = PR + ROWB;
   static constexpr int BYTES = APR + ROWB;
 };
-constexpr int kSpmmStages = 3;
 constexpr int kSpmmConsumers = kThreads;           // 8 consumer warps
 constexpr int kSpmmThreads = kThreads + 32;        // plus one producer warp
 
@@ -110,7 +113,7 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm_w(SpmmArgs<T> a) {
   constexpr int G = Sh::G, S = Sh::S, TEAM = Sh::TEAM, RPW = Sh::RPW, BT = Sh::BATCH;
   constexpr int NW = kSpmmConsumers / 32;
   constexpr int TEAMS = NW * RPW;
-  constexpr int ST = kSpmmStages;
+  constexpr int ST = Tl::ST;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
   uint64_t* empty = full + ST;
@@ -150,16 +153,21 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm_w(SpmmArgs<T> a) {
   if (wid == NW) {
     // ---------------- producer warp (one thread) ----------------
     if (lane == 0) {
+      // the end of the next tile is loaded one iteration early, so that its latency overlaps
+      // the wait for a free stage instead of delaying the copies
+      int64_t pb = my > 0 ? a.ptr[t0 * Tl::R] : 0;
+      int64_t pe_next = my > 0 ? a.ptr[min(a.n, (t0 + 1) * Tl::R)] : 0;
       int i = 0;
       for (; i < my; ++i) {
         const int s = i % ST;
+        const int64_t pe = pe_next;
+        if (i + 1 < my) pe_next = a.ptr[min(a.n, (t0 + i + 2) * Tl::R)];
         if (i >= ST && !mbar_wait(&empty[s], (uint32_t)((i / ST) - 1) & 1u)) {
           if (a.st) { a.st->err = MGE_ETIMEOUT; a.st->bad_stage = 6; a.st->done = DONE_ERROR; }
           break;
         }
         const int64_t r0 = (t0 + i) * Tl::R;
         const int rows = (int)min((int64_t)Tl::R, a.n - r0);
-        const int64_t pb = a.ptr[r0], pe = a.ptr[r0 + rows];
         const bool staged = pe - pb <= Tl::CAP;
         constexpr int VE = 16 / (int)sizeof(T);              // values per 16 bytes
         const int64_t c0 = pb & ~(int64_t)3, c1 = (pe + 3) & ~(int64_t)3;
@@ -193,6 +201,7 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm_w(SpmmArgs<T> a) {
           bulk_g2s(sb + Tl::AXR, a.cd + r0 * M, br, &full[s]);
           bulk_g2s(sb + Tl::PR, a.cdinv + r0, bd, &full[s]);
         }
+        pb = pe;
       }
       // no copy may still be landing when the block's shared memory is released
       for (int u = max(0, i - ST); u < i; ++u) mbar_wait(&full[u % ST], (uint32_t)(u / ST) & 1u);
@@ -228,33 +237,64 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm_w(SpmmArgs<T> a) {
         ld4(sWr + r * M + c0, wi);
         const int64_t pb = sptr[r];
         const int len = (int)(sptr[r + 1] - pb);
-        const int32_t* cp = staged ? scol + (pb - mc0) : a.col + pb;
-        const T* vp = staged ? sval + (pb - mv0) : a.val + pb;
-        // BATCH nonzeros per lane at a time: their indices and values, then their gathers
-        for (int k0 = sub; k0 < len; k0 += BT * S) {
+        // BATCH nonzeros per lane at a time: their indices and values, then their gathers;
+        // indices and values come from the stage (shared-memory loads) or, for tiles too
+        // dense to stage, from global memory
+        auto gather = [&](const int32_t* cp, const T* vp) {
+          // short rows are software-pipelined: the indices and gathers of batch b + 1 are
+          // issued before batch b is consumed, so a row's batches overlap instead of queueing
           int32_t j[BT];
-          T v[BT];
+          T v[BT], w[BT][4];
+          auto issue = [&](int k0, int32_t* jj, T* vv, T (*ww)[4]) {
 #pragma unroll
-          for (int b = 0; b < BT; ++b) {
-            const int k = k0 + b * S;
-            j[b] = k < len ? cp[k] : -1;
-            v[b] = k < len ? vp[k] : T(0);
-          }
-          T w[BT][4];
+            for (int b = 0; b < BT; ++b) {
+              const int k = k0 + b * S;
+              jj[b] = k < len ? cp[k] : -1;
+              vv[b] = k < len ? vp[k] : T(0);
+            }
 #pragma unroll
-          for (int b = 0; b < BT; ++b) {
-            if (j[b] >= 0) {
-              ldg4(a.Wr + (size_t)j[b] * M + c0, w[b]);
-            } else {
+            for (int b = 0; b < BT; ++b) {
+              if (jj[b] >= 0) {
+                ldg4(a.Wr + (size_t)jj[b] * M + c0, ww[b]);
+              } else {
 #pragma unroll
-              for (int q = 0; q < 4; ++q) w[b][q] = wi[q];
+                for (int q = 0; q < 4; ++q) ww[b][q] = wi[q];
+              }
+            }
+          };
+          if constexpr (SHORT) {
+            issue(sub, j, v, w);
+            for (int k0 = sub; k0 < len; k0 += BT * S) {
+              int32_t jn[BT];
+              T vn[BT], wn[BT][4];
+              const bool more = k0 + BT * S < len;
+              if (more) issue(k0 + BT * S, jn, vn, wn);
+#pragma unroll
+              for (int b = 0; b < BT; ++b)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] += v[b] * (w[b][q] - wi[q]);
+              if (more) {
+#pragma unroll
+                for (int b = 0; b < BT; ++b) {
+                  v[b] = vn[b];
+#pragma unroll
+                  for (int q = 0; q < 4; ++q) w[b][q] = wn[b][q];
+                }
+              }
+            }
+          } else {
+            // long rows: each lane's share of a row is about one batch
+            for (int k0 = sub; k0 < len; k0 += BT * S) {
+              issue(k0, j, v, w);
+#pragma unroll
+              for (int b = 0; b < BT; ++b)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] += v[b] * (w[b][q] - wi[q]);
             }
           }
-#pragma unroll
-          for (int b = 0; b < BT; ++b)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] += v[b] * (w[b][q] - wi[q]);
-        }
+        };
+        if (staged) gather(scol + (pb - mc0), sval + (pb - mv0));
+        else gather(a.col + pb, a.val + pb);
       }
       const bool lead = valid && sub == 0;
       if (!fused || !REG) {
@@ -406,12 +446,12 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm_w(SpmmArgs<T> a) {
         __syncwarp();
       }
     }
-    mbar_arrive(&empty[s]);      // this thread is done with stage s
+    mbar_arrive(&empty[s]);      // this thread is done with stage s (no lane-dependent branch)
   }
 }
 
 template <typename T, int M, bool SHORT>
-size_t spmm_smem() { return 256 + (size_t)kSpmmStages * SpmmTile<T, M, SHORT>::BYTES; }
+size_t spmm_smem() { return 256 + (size_t)SpmmTile<T, M, SHORT>::ST * SpmmTile<T, M, SHORT>::BYTES; }
 
 // rows short enough for the halved split: at most half a batch of nonzeros on average
 template <int M>

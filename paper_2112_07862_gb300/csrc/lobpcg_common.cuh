@@ -133,13 +133,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
                : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
   return done != 0;
 }
+// The same, suspending the thread until the phase completes or about ns nanoseconds pass:
+// a waiting thread issues no instructions meanwhile.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, uint32_t parity, uint32_t ns) {
+  uint32_t done;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(done) : "r"(smem_u32(bar)), "r"(parity), "r"(ns) : "memory");
+  return done != 0;
+}
 // Waits for the phase with the given parity to complete; gives up (false) after about
 // max_cycles SM cycles so that a lost copy cannot hang the GPU.
 constexpr long long kWaitCycles = 1ll << 31;
+// Waiting threads are suspended by the hardware between polls (a spinning wait took most of
+// the issue slots of the SM from the CTAs that had their data).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long max_cycles = kWaitCycles) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
+  while (!mbar_try_wait_suspend(bar, parity, 1000000u))
     if (clock64() - t0 > max_cycles) return false;
   return true;
 }
