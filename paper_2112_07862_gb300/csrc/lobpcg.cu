@@ -86,8 +86,11 @@ struct SpmmTile {
   static constexpr int VAL = COL + up((CAP + 8) * 4);
   static constexpr int ROWB = up(R * M * (int)sizeof(T));
   static constexpr int WR = VAL + up((CAP + 8) * (int)sizeof(T));
-  static constexpr int XR = WR + ROWB, AXR = XR + ROWB, PR = AXR + ROWB, APR = PR + ROWB;
-  static constexpr int BYTES = APR + ROWB;
+  // the short variant never runs the fused epilogue (no X, AX, P, AP rows): its stage holds
+  // W_raw (the iterate), R and d (XR, AXR) and D^-1 (PR) only
+  static constexpr int XR = WR + ROWB, AXR = XR + ROWB, PR = AXR + ROWB;
+  static constexpr int APR = PR + (SHORT ? up(R * (int)sizeof(T)) : ROWB);
+  static constexpr int BYTES = APR + (SHORT ? 0 : ROWB);
 };
 constexpr int kSpmmConsumers = kThreads;           // 8 consumer warps
 constexpr int kSpmmThreads = kThreads + 32;        // plus one producer warp
@@ -127,7 +130,9 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm_w(SpmmArgs<T> a) {
   constexpr int CS = M + 4;
   __shared__ __align__(16) T sMxLt[M * CS], sMpLt[M * CS], sLt[M * CS];
   __shared__ T scL[M];
-  __shared__ __align__(16) T sW[REG ? 1 : NW][RPW][M], sAW[REG ? 1 : NW][RPW][M];
+  // row vectors of the shared-memory epilogue (fused mode, long variant only)
+  __shared__ __align__(16) T sW[(REG || SHORT) ? 1 : NW][(REG || SHORT) ? 1 : RPW][M];
+  __shared__ __align__(16) T sAW[(REG || SHORT) ? 1 : NW][(REG || SHORT) ? 1 : RPW][M];
   const bool fused = a.sm != nullptr;
   const bool hx = fused && a.X, hp = fused && a.P;
   const bool cheb = !fused && a.cheb != 0;
@@ -262,34 +267,30 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm_w(SpmmArgs<T> a) {
               }
             }
           };
+          auto consume = [&](const T* vv, const T (*ww)[4]) {
+#pragma unroll
+            for (int b = 0; b < BT; ++b)
+#pragma unroll
+              for (int q = 0; q < 4; ++q) acc[q] += vv[b] * (ww[b][q] - wi[q]);
+          };
           if constexpr (SHORT) {
+            // two register sets in turn, so that no batch is copied from one set to the other
+            int32_t jn[BT];
+            T vn[BT], wn[BT][4];
             issue(sub, j, v, w);
-            for (int k0 = sub; k0 < len; k0 += BT * S) {
-              int32_t jn[BT];
-              T vn[BT], wn[BT][4];
-              const bool more = k0 + BT * S < len;
-              if (more) issue(k0 + BT * S, jn, vn, wn);
-#pragma unroll
-              for (int b = 0; b < BT; ++b)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[q] += v[b] * (w[b][q] - wi[q]);
-              if (more) {
-#pragma unroll
-                for (int b = 0; b < BT; ++b) {
-                  v[b] = vn[b];
-#pragma unroll
-                  for (int q = 0; q < 4; ++q) w[b][q] = wn[b][q];
-                }
-              }
+            for (int k0 = sub; k0 < len; k0 += 2 * BT * S) {
+              const int k1 = k0 + BT * S, k2 = k1 + BT * S;
+              if (k1 < len) issue(k1, jn, vn, wn);
+              consume(v, w);
+              if (k1 >= len) break;
+              if (k2 < len) issue(k2, j, v, w);
+              consume(vn, wn);
             }
           } else {
             // long rows: each lane's share of a row is about one batch
             for (int k0 = sub; k0 < len; k0 += BT * S) {
               issue(k0, j, v, w);
-#pragma unroll
-              for (int b = 0; b < BT; ++b)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[q] += v[b] * (w[b][q] - wi[q]);
+              consume(v, w);
             }
           }
         };
@@ -1110,7 +1111,7 @@ struct Solver {
     s.W = W.p; s.AW = AW.p;
     s.st = state;
     if (timed) MGE_TRY(time_begin(spmm_bytes(hx, hp)));
-    spmm_launch<T, M>(ctx, st, s, spmm_short<M>(nnz_a, n));
+    spmm_launch<T, M>(ctx, st, s, false);      // the fused epilogue runs in the long variant
     MGE_LAUNCHED(ctx, 1);
     if (timed) MGE_TRY(time_end());
     return MGE_OK;
