@@ -111,6 +111,11 @@ typedef struct {
   void*    stream;            /* cudaStream_t or NULL                                       */
   int      eps_precond_degree; /* Chebyshev preconditioner degree of the eps solve (see
                                  mge_embed_opts.precond_degree; 0 = default 24)              */
+  int      keep_order;        /* 0 (default): the library renumbers the nodes internally into
+                                 a locality order (compact patches of the graph in
+                                 consecutive rows, so that the SpMMs' gathers share cache
+                                 lines); every API call still takes and returns arrays in
+                                 the caller's node order.  1: keep the caller's numbering.   */
 } mge_ops_opts;
 
 /* Builds the operators of Sec. 4 for the graph W (n nodes, CSR as described above; host
@@ -155,6 +160,11 @@ mge_status mge_ops_info(const mge_ops* ops, mge_ops_info_t* out);
 mge_status mge_ops_export(const mge_ops* ops, int64_t* a_ptr, int32_t* a_col, double* a_val,
                           int64_t* q_ptr, int32_t* q_col, double* q_val, double* b,
                           int32_t* T, int on_device);
+
+/* The library's node order (see mge_ops_opts.keep_order): order[r] = the caller's node
+ * held in row r of the device-resident operators, r < n (the identity when the caller's
+ * order was kept).  order: int32 [n], host or device per on_device.  Errors: MGE_EINVAL. */
+mge_status mge_ops_node_order(const mge_ops* ops, int32_t* order, int on_device);
 
 /* Y = A X (which = 0) or Y = Q X (which = 1) with the library's SpMM kernel in the given
  * precision; X and Y are row-major [n x m] blocks of that precision (double, float, or

@@ -1,6 +1,9 @@
 // C ABI entry points of libmge (declared in include/mge.h).
 #include "mge_internal.cuh"
 
+#include <algorithm>
+#include <vector>
+
 #include <cstdarg>
 #include <cstring>
 
@@ -187,6 +190,29 @@ mge_status mge_ops_info(const mge_ops* o, mge_ops_info_t* out) {
   return MGE_OK;
 }
 
+// CSR of an operator in the library's node order -> the caller's order (host arrays): row i
+// is internal row rank[i], columns renamed by order and sorted ascending
+static void csr_to_caller(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& col,
+                          const std::vector<double>& val, const std::vector<int32_t>& order,
+                          const std::vector<int32_t>& rank, std::vector<int64_t>& rp2, std::vector<int32_t>& col2,
+                          std::vector<double>& val2) {
+  rp2.assign(n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) rp2[i + 1] = rp2[i] + (rp[rank[i] + 1] - rp[rank[i]]);
+  col2.resize(col.size());
+  val2.resize(val.size());
+  std::vector<std::pair<int32_t, double>> row;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t s = rp[rank[i]], e = rp[rank[i] + 1];
+    row.clear();
+    for (int64_t p = s; p < e; ++p) row.emplace_back(order[col[p]], val.empty() ? 0.0 : val[p]);
+    std::sort(row.begin(), row.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+    for (size_t k = 0; k < row.size(); ++k) {
+      col2[rp2[i] + k] = row[k].first;
+      if (!val2.empty()) val2[rp2[i] + k] = row[k].second;
+    }
+  }
+}
+
 mge_status mge_ops_export(const mge_ops* o, int64_t* a_ptr, int32_t* a_col, double* a_val, int64_t* q_ptr,
                           int32_t* q_col, double* q_val, double* b, int32_t* T, int on_device) {
   if (!o) return MGE_EINVAL;
@@ -195,14 +221,93 @@ mge_status mge_ops_export(const mge_ops* o, int64_t* a_ptr, int32_t* a_col, doub
   cudaSetDevice(ctx->device);
   cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   cudaStream_t st = ctx->closed ? nullptr : ctx->stream;
-  if (a_ptr) MGE_CUDA(ctx, cudaMemcpyAsync(a_ptr, op.a_ptr.p, (op.n + 1) * sizeof(int64_t), k, st));
-  if (a_col && op.nnz_a) MGE_CUDA(ctx, cudaMemcpyAsync(a_col, op.a_col.p, op.nnz_a * sizeof(int32_t), k, st));
-  if (a_val && op.nnz_a) MGE_CUDA(ctx, cudaMemcpyAsync(a_val, op.a_val.p, op.nnz_a * sizeof(double), k, st));
-  if (q_ptr) MGE_CUDA(ctx, cudaMemcpyAsync(q_ptr, op.q_ptr.p, (op.n + 1) * sizeof(int64_t), k, st));
-  if (q_col && op.nnz_q) MGE_CUDA(ctx, cudaMemcpyAsync(q_col, op.q_col.p, op.nnz_q * sizeof(int32_t), k, st));
-  if (q_val && op.nnz_q) MGE_CUDA(ctx, cudaMemcpyAsync(q_val, op.q_val.p, op.nnz_q * sizeof(double), k, st));
-  if (b) MGE_CUDA(ctx, cudaMemcpyAsync(b, op.b.p, op.n * sizeof(double), k, st));
-  if (T) MGE_CUDA(ctx, cudaMemcpyAsync(T, op.T.p, op.n * sizeof(int32_t), k, st));
+  if (!op.order.p) {
+    if (a_ptr) MGE_CUDA(ctx, cudaMemcpyAsync(a_ptr, op.a_ptr.p, (op.n + 1) * sizeof(int64_t), k, st));
+    if (a_col && op.nnz_a) MGE_CUDA(ctx, cudaMemcpyAsync(a_col, op.a_col.p, op.nnz_a * sizeof(int32_t), k, st));
+    if (a_val && op.nnz_a) MGE_CUDA(ctx, cudaMemcpyAsync(a_val, op.a_val.p, op.nnz_a * sizeof(double), k, st));
+    if (q_ptr) MGE_CUDA(ctx, cudaMemcpyAsync(q_ptr, op.q_ptr.p, (op.n + 1) * sizeof(int64_t), k, st));
+    if (q_col && op.nnz_q) MGE_CUDA(ctx, cudaMemcpyAsync(q_col, op.q_col.p, op.nnz_q * sizeof(int32_t), k, st));
+    if (q_val && op.nnz_q) MGE_CUDA(ctx, cudaMemcpyAsync(q_val, op.q_val.p, op.nnz_q * sizeof(double), k, st));
+    if (b) MGE_CUDA(ctx, cudaMemcpyAsync(b, op.b.p, op.n * sizeof(double), k, st));
+    if (T) MGE_CUDA(ctx, cudaMemcpyAsync(T, op.T.p, op.n * sizeof(int32_t), k, st));
+    MGE_CUDA(ctx, cudaStreamSynchronize(st));
+    return MGE_OK;
+  }
+  // renumbered operators: bring them to the host and rename them into the caller's order
+  const int64_t n = op.n;
+  std::vector<int32_t> order(n), rank(n);
+  MGE_CUDA(ctx, cudaMemcpyAsync(order.data(), op.order.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  MGE_CUDA(ctx, cudaMemcpyAsync(rank.data(), op.rank.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  auto fetch = [&](const int64_t* dp, const int32_t* dc, const double* dv, int64_t nnz, std::vector<int64_t>& rp,
+                   std::vector<int32_t>& c, std::vector<double>& v) -> mge_status {
+    rp.resize(n + 1); c.resize(nnz); v.resize(nnz);
+    MGE_CUDA(ctx, cudaMemcpyAsync(rp.data(), dp, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    if (nnz) {
+      MGE_CUDA(ctx, cudaMemcpyAsync(c.data(), dc, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      MGE_CUDA(ctx, cudaMemcpyAsync(v.data(), dv, nnz * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    MGE_CUDA(ctx, cudaStreamSynchronize(st));
+    return MGE_OK;
+  };
+  auto put = [&](void* dst, const void* src, size_t bytes) -> mge_status {
+    if (!dst || !bytes) return MGE_OK;
+    MGE_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st));
+    return MGE_OK;
+  };
+  std::vector<int64_t> rp, rp2;
+  std::vector<int32_t> c, c2;
+  std::vector<double> v, v2;
+  if (a_ptr || a_col || a_val) {
+    MGE_TRY(fetch(op.a_ptr.p, op.a_col.p, op.a_val.p, op.nnz_a, rp, c, v));
+    csr_to_caller(n, rp, c, v, order, rank, rp2, c2, v2);
+    MGE_TRY(put(a_ptr, rp2.data(), (n + 1) * sizeof(int64_t)));
+    MGE_TRY(put(a_col, c2.data(), op.nnz_a * sizeof(int32_t)));
+    MGE_TRY(put(a_val, v2.data(), op.nnz_a * sizeof(double)));
+    MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  }
+  if (q_ptr || q_col || q_val) {
+    MGE_TRY(fetch(op.q_ptr.p, op.q_col.p, op.q_val.p, op.nnz_q, rp, c, v));
+    csr_to_caller(n, rp, c, v, order, rank, rp2, c2, v2);
+    MGE_TRY(put(q_ptr, rp2.data(), (n + 1) * sizeof(int64_t)));
+    MGE_TRY(put(q_col, c2.data(), op.nnz_q * sizeof(int32_t)));
+    MGE_TRY(put(q_val, v2.data(), op.nnz_q * sizeof(double)));
+    MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  }
+  if (b) {
+    std::vector<double> bi(n), bo(n);
+    MGE_CUDA(ctx, cudaMemcpyAsync(bi.data(), op.b.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MGE_CUDA(ctx, cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < n; ++i) bo[i] = bi[rank[i]];
+    MGE_TRY(put(b, bo.data(), n * sizeof(double)));
+    MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  }
+  if (T) {
+    std::vector<int32_t> ti(n), to(n);
+    MGE_CUDA(ctx, cudaMemcpyAsync(ti.data(), op.T.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MGE_CUDA(ctx, cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < n; ++i) to[i] = ti[rank[i]];
+    MGE_TRY(put(T, to.data(), n * sizeof(int32_t)));
+    MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  }
+  return MGE_OK;
+}
+
+mge_status mge_ops_node_order(const mge_ops* o, int32_t* order, int on_device) {
+  if (!o || !order) return MGE_EINVAL;
+  const Ops& op = o->impl;
+  Ctx* ctx = op.ctx;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->closed ? nullptr : ctx->stream;
+  if (op.order.p) {
+    MGE_CUDA(ctx, cudaMemcpyAsync(order, op.order.p, op.n * sizeof(int32_t),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    MGE_CUDA(ctx, cudaStreamSynchronize(st));
+    return MGE_OK;
+  }
+  std::vector<int32_t> id(op.n);
+  for (int64_t i = 0; i < op.n; ++i) id[i] = (int32_t)i;
+  MGE_CUDA(ctx, cudaMemcpyAsync(order, id.data(), op.n * sizeof(int32_t),
+                                on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st));
   MGE_CUDA(ctx, cudaStreamSynchronize(st));
   return MGE_OK;
 }
@@ -210,6 +315,8 @@ mge_status mge_ops_export(const mge_ops* o, int64_t* a_ptr, int32_t* a_col, doub
 static LobOp make_op(const Ops& op, int which, int precision) {
   LobOp l;
   l.n = op.n;
+  l.row_order = op.order.p;
+  l.row_rank = op.rank.p;
   bool dbl = precision == MGE_FP64;
   if (which == 0) {
     l.ptr = op.a_ptr.p; l.col = op.a_col.p;
@@ -226,6 +333,11 @@ static LobOp make_op(const Ops& op, int which, int precision) {
       l.pc_shift = op.eps;
       l.pc_dinv = dbl ? (const void*)op.l_dinv.p : (const void*)op.l_dinv32.p;
       l.pc_beta = op.beta_l;
+      if (op.l_sl.built()) {
+        l.sl_slp = op.l_sl.slp.p; l.sl_perm = op.l_sl.perm.p; l.sl_col = op.l_sl.col.p;
+        l.sl_val = dbl ? (const void*)op.l_sl.val.p : (const void*)op.l_sl.val32.p;
+        l.sl_max_tile_slots = op.l_sl.max_tile_slots;
+      }
     }
   } else {
     l.ptr = op.q_ptr.p; l.col = op.q_col.p;
@@ -233,6 +345,11 @@ static LobOp make_op(const Ops& op, int which, int precision) {
     l.shift = 0.0; l.b = nullptr;
     l.dinv = dbl ? (const void*)op.dinv_q.p : (const void*)op.dinv_q32.p;
     l.norm = op.norm_q; l.bmax = 1.0; l.deflate = true; l.beta = op.beta_q;
+    if (op.q_sl.built()) {
+      l.sl_slp = op.q_sl.slp.p; l.sl_perm = op.q_sl.perm.p; l.sl_col = op.q_sl.col.p;
+      l.sl_val = dbl ? (const void*)op.q_sl.val.p : (const void*)op.q_sl.val32.p;
+      l.sl_max_tile_slots = op.q_sl.max_tile_slots;
+    }
   }
   return l;
 }

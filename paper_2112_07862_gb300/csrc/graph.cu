@@ -527,11 +527,124 @@ __global__ void k_fill_proxy(int64_t n, const int64_t* __restrict__ rp, const do
 
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
+// ---------------------------------------------------------------------------------------
+// sliced copy of a CSR operator (layout in mge_internal.cuh)
+// ---------------------------------------------------------------------------------------
+// One CTA per tile: the sorted position of each row (longest first, ties by row), and the
+// padded slot count of each slice
+__global__ void __launch_bounds__(kSliceTileRows) k_slice_rank(int64_t n, const int64_t* __restrict__ rp,
+                                                               uint8_t* __restrict__ perm, int64_t* __restrict__ cnt,
+                                                               unsigned long long* __restrict__ max_tile) {
+  __shared__ int64_t len[kSliceTileRows];
+  __shared__ int64_t sorted_len[kSliceTileRows];
+  __shared__ unsigned long long tile_slots;
+  const int64_t t = blockIdx.x;
+  const int r = threadIdx.x;
+  const int64_t row = t * kSliceTileRows + r;
+  const int64_t l = row < n ? rp[row + 1] - rp[row] : -1;
+  len[r] = l;
+  if (r == 0) tile_slots = 0;
+  __syncthreads();
+  int rank = 0;
+  for (int q = 0; q < kSliceTileRows; ++q) {
+    const int64_t lq = len[q];
+    rank += (lq > l) || (lq == l && q < r);
+  }
+  perm[t * kSliceTileRows + rank] = row < n ? (uint8_t)r : (uint8_t)0xFF;
+  sorted_len[rank] = l;
+  __syncthreads();
+  if (r < kSlicesPerTile) {
+    const int64_t m = sorted_len[r * kSliceRows] > 0 ? sorted_len[r * kSliceRows] : 0;
+    const int64_t c = (int64_t)kSliceRows * ((m + 3) & ~(int64_t)3);
+    cnt[t * kSlicesPerTile + r] = c;
+    atomicAdd(&tile_slots, (unsigned long long)c);
+  }
+  __syncthreads();
+  if (r == 0) atomicMax(max_tile, tile_slots);
+}
+
+// One thread per sorted position: its row's entries and padding, in slot order
+__global__ void k_slice_fill(int64_t ntiles, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                             const double* __restrict__ val, const float* __restrict__ val32,
+                             const uint8_t* __restrict__ perm, const int64_t* __restrict__ slp,
+                             int32_t* __restrict__ scol, double* __restrict__ sval, float* __restrict__ sval32) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= ntiles * kSliceTileRows) return;
+  const int64_t t = p / kSliceTileRows, s = p / kSliceRows;
+  const int q = (int)(p % kSliceRows);
+  const int64_t base = slp[s];
+  const int64_t plen = (slp[s + 1] - base) / kSliceRows;
+  if (plen == 0) return;
+  const int lr = perm[p];
+  // the slice's first row is its longest, so it exists whenever the slice has slots
+  const int32_t pad = (int32_t)(t * kSliceTileRows + perm[s * kSliceRows]);
+  int64_t b = 0, len = 0;
+  if (lr != 0xFF) {
+    b = rp[t * kSliceTileRows + lr];
+    len = rp[t * kSliceTileRows + lr + 1] - b;
+  }
+  for (int64_t k = 0; k < plen; ++k) {
+    const int64_t d = base + (k >> 2) * (4 * kSliceRows) + q * 4 + (k & 3);
+    const bool in = k < len;
+    scol[d] = in ? col[b + k] : pad;
+    sval[d] = in ? val[b + k] : 0.0;
+    sval32[d] = in ? val32[b + k] : 0.0f;
+  }
+}
+
+// Builds the sliced copy of (rp, col, val, val32); leaves `out` unbuilt when the padding
+// would more than double the entries (a few very long rows among short ones)
+mge_status build_sliced(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* rp, const int32_t* col,
+                        const double* val, const float* val32, int64_t nnz, Sliced* out) {
+  const int64_t ntiles = (n + kSliceTileRows - 1) / kSliceTileRows;
+  const int64_t ns = ntiles * kSlicesPerTile;
+  DevBuf<int64_t> slp, cnt;
+  DevBuf<uint8_t> perm;
+  DevBuf<unsigned long long> mx;
+  MGE_TRY(slp.alloc(ctx, ns + 4));
+  MGE_TRY(perm.alloc(ctx, ntiles * kSliceTileRows));
+  MGE_TRY(cnt.alloc(ctx, ns));
+  MGE_TRY(mx.alloc(ctx, 1));
+  MGE_CUDA(ctx, cudaMemsetAsync(mx.p, 0, sizeof(unsigned long long), st));
+  k_slice_rank<<<(unsigned)ntiles, kSliceTileRows, 0, st>>>(n, rp, perm.p, cnt.p, mx.p);
+  MGE_LAUNCHED(ctx, 1);
+  MGE_CUDA(ctx, cudaGetLastError());
+  MGE_TRY(exclusive_scan(ctx, st, cnt.p, ns, slp.p));     // synchronises the stream
+  int64_t slots = 0;
+  unsigned long long h_mx = 0;
+  MGE_CUDA(ctx, cudaMemcpyAsync(&slots, slp.p + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  MGE_CUDA(ctx, cudaMemcpyAsync(&h_mx, mx.p, sizeof(h_mx), cudaMemcpyDeviceToHost, st));
+  MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  if (slots > 2 * nnz + 4 * (int64_t)kSliceRows * ns) return MGE_OK;
+  const int64_t tail[3] = {slots, slots, slots};
+  MGE_CUDA(ctx, cudaMemcpyAsync(slp.p + ns + 1, tail, sizeof(tail), cudaMemcpyHostToDevice, st));
+  MGE_TRY(out->col.alloc(ctx, slots));
+  MGE_TRY(out->val.alloc(ctx, slots));
+  MGE_TRY(out->val32.alloc(ctx, slots));
+  if (slots > 0) {
+    k_slice_fill<<<grid_for(ntiles * kSliceTileRows, 256), 256, 0, st>>>(ntiles, rp, col, val, val32, perm.p, slp.p,
+                                                                          out->col.p, out->val.p, out->val32.p);
+    MGE_LAUNCHED(ctx, 1);
+  }
+  MGE_CUDA(ctx, cudaGetLastError());
+  MGE_CUDA(ctx, cudaStreamSynchronize(st));   // `tail` is a host array on this frame
+  out->ntiles = ntiles;
+  out->slots = slots;
+  out->max_tile_slots = (int64_t)h_mx;
+  std::swap(out->slp.p, slp.p); std::swap(out->slp.n, slp.n); out->slp.ctx = ctx;
+  std::swap(out->perm.p, perm.p); std::swap(out->perm.n, perm.n); out->perm.ctx = ctx;
+  return MGE_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------------------
+mge_status scan_exclusive(Ctx* ctx, cudaStream_t st, const int64_t* in, int64_t n, int64_t* out) {
+  return exclusive_scan(ctx, st, in, n, out);
+}
+
 mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* rp_in,
                                 const int32_t* col_in, const double* w_in, int on_device,
                                 const mge_ops_opts* opts, Ops* ops) {
@@ -616,6 +729,21 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
   MGE_CUDA(ctx, cudaStreamSynchronize(st));
   if (h_err & ERR_ASYM) { set_error(ctx, "W is not symmetric"); return MGE_ENOTSYM; }
 
+  // --- node order: everything below runs on W renamed into the locality order ---
+  if (!o.keep_order && n > 1) {
+    DevBuf<int64_t> rp2;
+    DevBuf<int32_t> col2;
+    DevBuf<double> w2;
+    MGE_TRY(locality_order(ctx, st, n, ops->w_ptr.p, ops->w_col.p, ops->w_val.p, nnz, &ops->order, &ops->rank,
+                           &rp2, &col2, &w2));
+    std::swap(ops->w_ptr.p, rp2.p); std::swap(ops->w_ptr.n, rp2.n);
+    std::swap(ops->w_col.p, col2.p); std::swap(ops->w_col.n, col2.n);
+    std::swap(ops->w_val.p, w2.p); std::swap(ops->w_val.n, w2.n);
+    rp = ops->w_ptr.p;
+    col = ops->w_col.p;
+    w = ops->w_val.p;
+  }
+
   // --- two-hop sets ---
   DevBuf<int64_t> cnt, U;
   DevBuf<int32_t> big_list;
@@ -682,6 +810,8 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
                                           ops->q_val.p, ops->q_val32.p, ops->dinv_q.p, ops->dinv_q32.p,
                                           den_max, normq, beta_q);
   MGE_LAUNCHED(ctx, 1);
+  MGE_TRY(build_sliced(ctx, st, n, ops->q_ptr.p, ops->q_col.p, ops->q_val.p, ops->q_val32.p, ops->nnz_q,
+                       &ops->q_sl));
 
   // --- components of the two-hop graph (eps = 0 when more than one) ---
   {
@@ -716,6 +846,11 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
       qop.dinv = (o.precision == MGE_FP64) ? (const void*)ops->dinv_q.p : (const void*)ops->dinv_q32.p;
       qop.norm = ops->norm_q; qop.bmax = 1.0; qop.deflate = true; qop.beta = ops->beta_q;
       qop.precond_degree = o.eps_precond_degree > 0 ? std::min(o.eps_precond_degree, 64) : kDefaultPrecondDegree;
+      if (ops->q_sl.built()) {
+        qop.sl_slp = ops->q_sl.slp.p; qop.sl_perm = ops->q_sl.perm.p; qop.sl_col = ops->q_sl.col.p;
+        qop.sl_val = (o.precision == MGE_FP64) ? (const void*)ops->q_sl.val.p : (const void*)ops->q_sl.val32.p;
+        qop.sl_max_tile_slots = ops->q_sl.max_tile_slots;
+      }
       int guard = o.eps_guard > 0 ? o.eps_guard : 3;
       int m = round_block_width(1 + guard);
       if (m > n - 1) m = -1;
@@ -814,6 +949,7 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
     MGE_CUDA(ctx, cudaMemcpyAsync(&h_bl, beta_l, sizeof(double), cudaMemcpyDeviceToHost, st));
     MGE_CUDA(ctx, cudaStreamSynchronize(st));
     ops->beta_l = h_bl > 0 ? h_bl : 2.0;
+    MGE_TRY(build_sliced(ctx, st, n, ops->w_ptr.p, ops->w_col.p, ops->l_val.p, ops->l_val32.p, nnz_w, &ops->l_sl));
   }
   if (h_err & ERR_ISOLATED) {
     set_error(ctx, "isolated node: a Gershgorin radius r_i is zero, so B is singular");

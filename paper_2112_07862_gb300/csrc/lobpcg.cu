@@ -45,6 +45,8 @@ struct SpmmArgs {
   const T* X; const T* AX; const T* P; const T* AP;   // NULL when absent
   const SmallT<T>* sm;                                 // L, M_x L, M_p L, c L (NULL: plain A*Wr)
   T* W; T* AW;
+  const int32_t* out_row;    // plain product only: row r of the result goes to row out_row[r]
+                             // of AW (NULL: row r)
   State* st;
   int tiles_per_cta;
   // one step of the Chebyshev preconditioner (cheb != 0; Wr is then the iterate x_k):
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm_w(SpmmArgs<T> a) {
             st4(a.cd_out + row * M + c0, dn);
             st4(a.cx_out + row * M + c0, xn);
           } else {
-            st4(a.AW + row * M + c0, y);
+            st4(a.AW + (a.out_row ? (int64_t)a.out_row[row] : row) * M + c0, y);
           }
         }
         continue;
@@ -880,14 +882,15 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 }
 
 template <typename T>
-__global__ void k_init_block(int64_t n, int M, uint64_t seed, const double* x0, int x0_cols, T* Wr) {
+__global__ void k_init_block(int64_t n, int M, uint64_t seed, const double* x0, int x0_cols,
+                             const int32_t* row_order, T* Wr) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n * M) return;
   int64_t i = t / M;
   int c = (int)(t % M);
   double v;
   if (x0 && c < x0_cols) {
-    v = x0[(int64_t)c * n + i];
+    v = x0[(int64_t)c * n + (row_order ? (int64_t)row_order[i] : i)];   // x0 is in the caller's order
   } else {
     // Box-Muller on two uniforms from the counter (i, c)
     uint64_t h1 = splitmix64(seed ^ splitmix64((uint64_t)t * 2));
@@ -911,24 +914,28 @@ __global__ void k_vmax(int64_t n, int M, int K, const T* X, unsigned long long* 
 
 template <typename T>
 __global__ void k_vidx(int64_t n, int M, int K, const T* X, const unsigned long long* vmax,
-                       unsigned long long* vidx) {
+                       const int32_t* row_order, unsigned long long* vidx) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n * K) return;
   int64_t i = t / K;
   int c = (int)(t % K);
   double v = fabs((double)X[i * M + c]);
-  if ((unsigned long long)__double_as_longlong(v) == vmax[c]) atomicMin(vidx + c, (unsigned long long)i);
+  // ties go to the smallest node index in the caller's order
+  const int64_t e = row_order ? (int64_t)row_order[i] : i;
+  if ((unsigned long long)__double_as_longlong(v) == vmax[c]) atomicMin(vidx + c, (unsigned long long)e);
 }
 
 template <typename T>
-__global__ void k_write_v(int64_t n, int M, int K, const T* X, const unsigned long long* vidx, double* V) {
+__global__ void k_write_v(int64_t n, int M, int K, const T* X, const unsigned long long* vidx,
+                          const int32_t* row_order, const int32_t* row_rank, double* V) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n * K) return;
   int c = (int)(t / n);
   int64_t i = t % n;
-  unsigned long long r = vidx[c];
-  double s = (r < (unsigned long long)n && (double)X[(int64_t)r * M + c] < 0.0) ? -1.0 : 1.0;
-  V[t] = s * (double)X[i * M + c];
+  unsigned long long r = vidx[c];                       // in the caller's order
+  const int64_t ri = (r < (unsigned long long)n) ? (row_rank ? (int64_t)row_rank[r] : (int64_t)r) : -1;
+  double s = (ri >= 0 && (double)X[ri * M + c] < 0.0) ? -1.0 : 1.0;
+  V[(int64_t)c * n + (row_order ? (int64_t)row_order[i] : i)] = s * (double)X[i * M + c];
 }
 
 inline unsigned gridn(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -1158,6 +1165,31 @@ struct Solver {
     double rho_prev = 1.0 / ch_sigma;
     for (int k = 1; k < cheb_deg; ++k) {
       const double rho = 1.0 / (2.0 * ch_sigma - rho_prev);
+      if (op.sl_slp) {
+        // the sliced copy of the operator (rows sorted and padded per slice)
+        ChebArgs<T> c{};
+        c.n = n;
+        c.slp = op.sl_slp; c.perm = op.sl_perm; c.col = op.sl_col;
+        c.val = static_cast<const T*>(op.sl_val);
+        c.shift = (T)(op.pc_ptr ? op.pc_shift : op.shift);
+        c.X = (k == 1) ? Wr.p : ys[k % 2];
+        c.R = Wr.p;
+        c.D = (k == 1) ? Wr.p : Dc.p;
+        c.dinv = static_cast<const T*>(op.pc_ptr ? op.pc_dinv : op.dinv);
+        c.Dout = Dc.p;
+        c.Xout = ys[(k + 1) % 2];
+        c.sy = (k == 1) ? (T)(1.0 / ch_theta) : T(1);
+        c.sd = (k == 1) ? (T)(1.0 / ch_theta) : T(1);
+        c.c1 = (T)(rho * rho_prev);
+        c.c2 = (T)(2.0 * rho / ch_delta);
+        c.st = state;
+        if (timed) MGE_TRY(time_begin(cheb_bytes()));
+        MGE_CUDA(ctx, (cheb_launch<T, M>(ctx, st, c, op.sl_max_tile_slots)));
+        MGE_LAUNCHED(ctx, 1);
+        if (timed) MGE_TRY(time_end());
+        rho_prev = rho;
+        continue;
+      }
       SpmmArgs<T> s{};
       s.n = n;
       if (op.pc_ptr) {
@@ -1240,7 +1272,7 @@ struct Solver {
     MGE_CUDA(ctx, cudaEventRecord(e0, st));
     const bool timed = ctx->timing;
     // --- init: W_raw = X0, normalise, Rayleigh-Ritz on span(W) ---
-    k_init_block<T><<<gridn(n * M, 256), 256, 0, st>>>(n, M, seed, x0, x0_cols, Wr.p);
+    k_init_block<T><<<gridn(n * M, 256), 256, 0, st>>>(n, M, seed, x0, x0_cols, op.row_order, Wr.p);
     MGE_LAUNCHED(ctx, 1);
     wsrc = Wr.p;
     launch_gram_w(false, false);
@@ -1346,8 +1378,8 @@ struct Solver {
       MGE_CUDA(ctx, cudaMemsetAsync(sm->vmax, 0, sizeof(sm->vmax), st));
       MGE_CUDA(ctx, cudaMemsetAsync(sm->vidx, 0xff, sizeof(sm->vidx), st));
       k_vmax<T><<<gridn(n * K, 256), 256, 0, st>>>(n, M, K, X.p, sm->vmax);
-      k_vidx<T><<<gridn(n * K, 256), 256, 0, st>>>(n, M, K, X.p, sm->vmax, sm->vidx);
-      k_write_v<T><<<gridn(n * K, 256), 256, 0, st>>>(n, M, K, X.p, sm->vidx, V_out);
+      k_vidx<T><<<gridn(n * K, 256), 256, 0, st>>>(n, M, K, X.p, sm->vmax, op.row_order, sm->vidx);
+      k_write_v<T><<<gridn(n * K, 256), 256, 0, st>>>(n, M, K, X.p, sm->vidx, op.row_order, op.row_rank, V_out);
       MGE_LAUNCHED(ctx, 3);
       MGE_CUDA(ctx, cudaGetLastError());
     }
@@ -1382,6 +1414,7 @@ mge_status solve_m(Ctx* ctx, cudaStream_t st, const LobOp& op, int K, double tol
   }
   MGE_CUDA(ctx, cudaFuncSetAttribute(k_gram<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
   MGE_CUDA(ctx, (spmm_configure<T, M>()));
+  MGE_CUDA(ctx, (cheb_configure<T, M>()));
   MGE_CUDA(ctx, rr_configure());
   return s.run(check_every, use_graph, seed, x0, x0_cols, V_out, res);
 }
@@ -1403,10 +1436,11 @@ mge_status solve_t(Ctx* ctx, cudaStream_t st, const LobOp& op, int K, int m, dou
 }
 
 template <typename T, int M>
-mge_status apply_m(Ctx* ctx, cudaStream_t st, const LobOp& op, const void* X, void* Y) {
+mge_status apply_m(Ctx* ctx, cudaStream_t st, const LobOp& op, const void* X, void* Y, const int32_t* out_row) {
   SpmmArgs<T> s{};
   s.n = op.n; s.ptr = op.ptr; s.col = op.col; s.val = static_cast<const T*>(op.val);
   s.shift = (T)op.shift; s.Wr = static_cast<const T*>(X); s.AW = static_cast<T*>(Y);
+  s.out_row = out_row;
   s.W = nullptr; s.sm = nullptr; s.st = nullptr;
   MGE_CUDA(ctx, (spmm_configure<T, M>()));
   int64_t nnz = 0;
@@ -1436,27 +1470,54 @@ mge_status lobpcg_solve(Ctx* ctx, cudaStream_t st, const LobOp& op, int precisio
   return MGE_EINVAL;
 }
 
-mge_status spmm_apply(Ctx* ctx, cudaStream_t st, const LobOp& op, int precision, int m, const void* X, void* Y) {
+// Y = A X with X already in the library's node order; row r of the product goes to row
+// out_row[r] of Y (NULL: row r)
+mge_status apply_internal(Ctx* ctx, cudaStream_t st, const LobOp& op, int precision, int m, const void* X, void* Y,
+                          const int32_t* out_row) {
   using namespace lob;
   if (precision == MGE_FP64) {
     switch (m) {
-      case 4: return apply_m<double, 4>(ctx, st, op, X, Y);
-      case 8: return apply_m<double, 8>(ctx, st, op, X, Y);
-      case 12: return apply_m<double, 12>(ctx, st, op, X, Y);
-      case 16: return apply_m<double, 16>(ctx, st, op, X, Y);
-      case 24: return apply_m<double, 24>(ctx, st, op, X, Y);
+      case 4: return apply_m<double, 4>(ctx, st, op, X, Y, out_row);
+      case 8: return apply_m<double, 8>(ctx, st, op, X, Y, out_row);
+      case 12: return apply_m<double, 12>(ctx, st, op, X, Y, out_row);
+      case 16: return apply_m<double, 16>(ctx, st, op, X, Y, out_row);
+      case 24: return apply_m<double, 24>(ctx, st, op, X, Y, out_row);
     }
   } else if (precision == MGE_FP32) {
     switch (m) {
-      case 4: return apply_m<float, 4>(ctx, st, op, X, Y);
-      case 8: return apply_m<float, 8>(ctx, st, op, X, Y);
-      case 12: return apply_m<float, 12>(ctx, st, op, X, Y);
-      case 16: return apply_m<float, 16>(ctx, st, op, X, Y);
-      case 24: return apply_m<float, 24>(ctx, st, op, X, Y);
+      case 4: return apply_m<float, 4>(ctx, st, op, X, Y, out_row);
+      case 8: return apply_m<float, 8>(ctx, st, op, X, Y, out_row);
+      case 12: return apply_m<float, 12>(ctx, st, op, X, Y, out_row);
+      case 16: return apply_m<float, 16>(ctx, st, op, X, Y, out_row);
+      case 24: return apply_m<float, 24>(ctx, st, op, X, Y, out_row);
     }
   }
   set_error(ctx, "unsupported precision %d / width %d for apply", precision, m);
   return MGE_EINVAL;
+}
+
+// rows of `vec` 16-byte vectors: dst row r = src row order[r]
+__global__ void k_gather_rows(int64_t n, int vec, const int32_t* __restrict__ order, const uint4* __restrict__ src,
+                              uint4* __restrict__ dst) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * vec) return;
+  const int64_t r = t / vec;
+  dst[t] = src[(int64_t)order[r] * vec + (t % vec)];
+}
+
+mge_status spmm_apply(Ctx* ctx, cudaStream_t st, const LobOp& op, int precision, int m, const void* X, void* Y) {
+  if (!op.row_order) return apply_internal(ctx, st, op, precision, m, X, Y, nullptr);
+  // X into the library's node order, the product back into the caller's
+  const size_t elem = precision == MGE_FP64 ? sizeof(double) : sizeof(float);
+  const int vec = (int)((size_t)m * elem / 16);
+  DevBuf<uint4> xi;
+  MGE_TRY(xi.alloc(ctx, (size_t)op.n * vec));
+  k_gather_rows<<<lob::gridn(op.n * vec, 256), 256, 0, st>>>(op.n, vec, op.row_order, static_cast<const uint4*>(X), xi.p);
+  MGE_LAUNCHED(ctx, 1);
+  MGE_CUDA(ctx, cudaGetLastError());
+  MGE_TRY(apply_internal(ctx, st, op, precision, m, xi.p, Y, op.row_order));
+  MGE_CUDA(ctx, cudaStreamSynchronize(st));     // xi is freed on return
+  return MGE_OK;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1505,8 +1566,17 @@ mge_status spmm_apply_inplace(Ctx* ctx, cudaStream_t st, const LobOp& op, int pr
     }
     scratch = g_inplace_addr[ctx->device];
   }
-  MGE_CUDA(ctx, cudaMemcpyAsync(scratch, XY, bytes, cudaMemcpyDeviceToDevice, st));
-  return spmm_apply(ctx, st, op, precision, m, scratch, XY);
+  if (op.row_order) {
+    // the copy is made in the library's node order; the product lands in the caller's
+    const int vec = (int)((size_t)m * elem / 16);
+    k_gather_rows<<<lob::gridn(op.n * vec, 256), 256, 0, st>>>(op.n, vec, op.row_order, static_cast<const uint4*>(XY),
+                                                          static_cast<uint4*>(scratch));
+    MGE_LAUNCHED(ctx, 1);
+    MGE_CUDA(ctx, cudaGetLastError());
+  } else {
+    MGE_CUDA(ctx, cudaMemcpyAsync(scratch, XY, bytes, cudaMemcpyDeviceToDevice, st));
+  }
+  return apply_internal(ctx, st, op, precision, m, scratch, XY, op.row_order);
 }
 
 }  // namespace mge

@@ -219,5 +219,36 @@ cudaError_t rr_configure();
 void launch_rr(cudaStream_t st, const RRArgs& a, bool inverse_form);
 void launch_wprep(cudaStream_t st, const WprepArgs& a, bool fp64);
 
+// One Chebyshev step of the LOBPCG preconditioner on the sliced copy of an operator (cheb.cu):
+//   y = A x (difference form),  z = R - dinv (sy y),  d_out = c1 (sd D) + c2 z,
+//   x_out = sy x + d_out.
+// X, R, D, Dout, Xout: [n x M] row-major; D and Dout may be the same array (each row of D is
+// read before the same row of Dout is written); dinv carries zeroed elements up to n rounded
+// up to 16 bytes.
+template <typename T>
+struct ChebArgs {
+  int64_t n;
+  const int64_t* slp;
+  const uint8_t* perm;
+  const int32_t* col;
+  const T* val;
+  T shift;
+  const T* X;
+  const T* R;
+  const T* D;
+  const T* dinv;
+  T* Dout;
+  T* Xout;
+  T sy, sd, c1, c2;
+  State* st;
+};
+
+// Launches the step on stream st; max_tile_slots (the densest tile of the sliced copy) sizes
+// the shared-memory stages.  cheb_configure raises the instances' dynamic shared-memory limit.
+template <typename T, int M>
+cudaError_t cheb_launch(const Ctx* ctx, cudaStream_t st, const ChebArgs<T>& a, int64_t max_tile_slots);
+template <typename T, int M>
+cudaError_t cheb_configure();
+
 }  // namespace lob
 }  // namespace mge

@@ -97,11 +97,40 @@ struct DevBuf {
 };
 
 // ---------------------------------------------------------------------------------------
+// Row-sorted, slice-padded copy of a CSR operator (the layout of the Chebyshev steps).
+// The rows of each tile of kSliceTileRows consecutive rows are sorted by length, longest
+// first, and cut into slices of kSliceRows sorted rows; every row of a slice is padded to the
+// slice's longest row rounded up to a multiple of 4 (padding: value 0, column = the slice's
+// first row, so that a padded term a (x_j - x_i) is exactly 0).  Slot k of the row at sorted
+// position q of slice s is element slp[s] + (k / 4) * 64 + q * 4 + k % 4: one 16-byte load
+// gives a row four consecutive slots, and the 16 rows' loads are contiguous.
+// ---------------------------------------------------------------------------------------
+constexpr int kSliceTileRows = 128;
+constexpr int kSliceRows = 16;
+constexpr int kSlicesPerTile = kSliceTileRows / kSliceRows;
+
+struct Sliced {
+  int64_t ntiles = 0, slots = 0;
+  int64_t max_tile_slots = 0;       // slots of the densest tile
+  DevBuf<int64_t> slp;              // [kSlicesPerTile * ntiles + 4]: first slot of each slice;
+                                    // the entries from index kSlicesPerTile * ntiles on = slots
+  DevBuf<uint8_t> perm;             // [kSliceTileRows * ntiles]: tile-local row at each sorted
+                                    // position, 0xFF past the last row
+  DevBuf<int32_t> col;              // [slots]
+  DevBuf<double> val;               // [slots]
+  DevBuf<float> val32;              // [slots]
+  bool built() const { return slp.p != nullptr; }
+};
+
+// ---------------------------------------------------------------------------------------
 // operators built by mge_build_graph_ops (everything device resident)
 // ---------------------------------------------------------------------------------------
 struct Ops {
   Ctx* ctx = nullptr;
   int64_t n = 0, nnz_w = 0, nnz_a = 0, nnz_q = 0;
+  // Every array below is in the library's node order: row r holds input node order[r]
+  // (order and rank empty: the input order).  The API translates at its boundary.
+  DevBuf<int32_t> order, rank;
   DevBuf<int64_t> w_ptr;  DevBuf<int32_t> w_col;  DevBuf<double> w_val;
   DevBuf<int32_t> T;
   DevBuf<int64_t> q_ptr;  DevBuf<int32_t> q_col;  DevBuf<double> q_val;
@@ -115,6 +144,9 @@ struct Ops {
   DevBuf<double>  l_val, l_dinv;
   DevBuf<float>   l_val32, l_dinv32;
   double beta_l = 2;
+  // sliced copies of Q (the eps solve's Chebyshev steps) and of L + eps I (the embedding's);
+  // left unbuilt when the padding would more than double the stored entries
+  Sliced q_sl, l_sl;
   double eps = 0, mu = 0, norm_a = 0, norm_q = 0, bmax = 1;
   double beta_a = 2, beta_q = 2;            // Gershgorin bounds of the spectra of D^-1 A, D^-1 Q
   int degenerate = 0, ncomp = 1, eps_iters = 0;
@@ -147,6 +179,17 @@ struct LobOp {
   double pc_shift = 0;
   const void* pc_dinv = nullptr;
   double pc_beta = 2;
+  // sliced copy of the operator the Chebyshev steps apply (NULL: they use its CSR form)
+  const int64_t* sl_slp = nullptr;
+  const uint8_t* sl_perm = nullptr;
+  const int32_t* sl_col = nullptr;
+  const void* sl_val = nullptr;     // double* or float* by precision
+  int64_t sl_max_tile_slots = 0;
+  // node order of the operator's rows (NULL: the caller's order): internal row r is caller
+  // row row_order[r], caller row i is internal row row_rank[i]; x0 and V are in the
+  // caller's order
+  const int32_t* row_order = nullptr;
+  const int32_t* row_rank = nullptr;
 };
 
 struct LobResult {
@@ -169,6 +212,16 @@ mge_status spmm_apply(Ctx* ctx, cudaStream_t st, const LobOp& op, int precision,
 // Y = A Y through a fixed device array (no allocation); see lobpcg.cu.
 mge_status spmm_apply_inplace(Ctx* ctx, cudaStream_t st, const LobOp& op, int precision, int m, void* XY);
 size_t inplace_scratch_bytes();
+
+// out[0..n] = exclusive scan of in[0..n-1], out[n] = the total (synchronises the stream)
+mge_status scan_exclusive(Ctx* ctx, cudaStream_t st, const int64_t* in, int64_t n, int64_t* out);
+
+// Locality order of the nodes of W (order.cu): order[r] = the input node placed at row r,
+// rank[i] = the row of input node i, and W renamed (rp_out, col_out, w_out; ascending
+// columns, the same padding as the input copy).
+mge_status locality_order(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* rp, const int32_t* col,
+                          const double* w, int64_t nnz, DevBuf<int32_t>* order, DevBuf<int32_t>* rank,
+                          DevBuf<int64_t>* rp_out, DevBuf<int32_t>* col_out, DevBuf<double>* w_out);
 
 // supported block widths
 inline int round_block_width(int m) {

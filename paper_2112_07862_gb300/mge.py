@@ -25,7 +25,7 @@ PRECISION = {"fp64": MGE_FP64, "fp32": MGE_FP32, "bf16": MGE_BF16}
 EXPORTS = [
     "mge_create", "mge_destroy", "mge_strerror", "mge_ctx_last_error", "mge_ctx_stats",
     "mge_ctx_set_timing", "mge_ctx_reset_stats", "mge_build_graph_ops", "mge_ops_destroy",
-    "mge_ops_info", "mge_ops_export", "mge_ops_apply", "mge_ops_apply_inplace", "mge_embed", "mge_submit", "mge_poll",
+    "mge_ops_info", "mge_ops_export", "mge_ops_node_order", "mge_ops_apply", "mge_ops_apply_inplace", "mge_embed", "mge_submit", "mge_poll",
     "mge_release",
 ]
 
@@ -39,7 +39,7 @@ class mge_ops_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("eps_override_set", C.c_int), ("eps_override", C.c_double),
                 ("mu_override_set", C.c_int), ("mu_override", C.c_double), ("eps_tol", C.c_double),
                 ("eps_guard", C.c_int), ("eps_maxiter", C.c_int), ("seed", C.c_uint64),
-                ("stream", C.c_void_p), ("eps_precond_degree", C.c_int)]
+                ("stream", C.c_void_p), ("eps_precond_degree", C.c_int), ("keep_order", C.c_int)]
 
 
 class mge_ops_info_t(C.Structure):
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH):
         "mge_ops_destroy": (i, [vp]),
         "mge_ops_info": (i, [vp, C.POINTER(mge_ops_info_t)]),
         "mge_ops_export": (i, [vp, vp, vp, vp, vp, vp, vp, vp, vp, i]),
+        "mge_ops_node_order": (i, [vp, vp, i]),
         "mge_ops_apply": (i, [vp, vp, i, i, i, vp, vp, vp]),
         "mge_ops_apply_inplace": (i, [vp, vp, i, i, i, vp, vp]),
         "mge_embed": (i, [vp, vp, i, d, C.POINTER(mge_embed_opts), vp, vp, C.POINTER(mge_embed_info)]),
@@ -207,6 +208,16 @@ def mge_ops_export(ops):
     return dict(a_ptr=a_ptr, a_col=a_col, a_val=a_val, q_ptr=q_ptr, q_col=q_col, q_val=q_val, b=b, T=T)
 
 
+def mge_ops_node_order(ops):
+    """The library's node order: order[r] = the caller's node in row r of the operators."""
+    n = mge_ops_info(ops).n
+    order = np.empty(n, np.int32)
+    s = load().mge_ops_node_order(ops, _ptr(order), 0)
+    if s != MGE_OK:
+        raise MgeError(s, "mge_ops_node_order")
+    return order
+
+
 def mge_ops_apply(ctx, ops, which: int, precision: int, m: int, X, Y, stream=None) -> int:
     """Y = A X (which=0) or Q X (which=1); X, Y torch CUDA tensors [n, m] row-major."""
     s = load().mge_ops_apply(ctx, ops, which, precision, m, _ptr(X), _ptr(Y), stream)
@@ -255,7 +266,7 @@ def mge_release(ctx, ticket: int) -> int:
 # ---- conveniences ------------------------------------------------------------------------
 
 def ops_opts(precision="fp32", eps=None, mu=None, eps_tol=0.0, seed=0, stream=None, eps_guard=0,
-             eps_maxiter=0, eps_precond_degree=0) -> mge_ops_opts:
+             eps_maxiter=0, eps_precond_degree=0, keep_order=False) -> mge_ops_opts:
     o = mge_ops_opts()
     o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     if eps is not None:
@@ -268,6 +279,7 @@ def ops_opts(precision="fp32", eps=None, mu=None, eps_tol=0.0, seed=0, stream=No
     o.seed = seed
     o.stream = stream
     o.eps_precond_degree = eps_precond_degree
+    o.keep_order = 1 if keep_order else 0
     return o
 
 
@@ -330,6 +342,9 @@ class Ops:
 
     def export(self):
         return mge_ops_export(self.h)
+
+    def node_order(self):
+        return mge_ops_node_order(self.h)
 
     def close(self):
         if self.h:
