@@ -163,7 +163,8 @@ def spmm_traffic_per_launch():
         return None
     try:
         d = json.load(open(path))
-        src = open(os.path.join(ROOT, "paper_2112_07862_gb300", "csrc", "lobpcg.cu"), "rb").read()
+        src = b"".join(open(os.path.join(ROOT, "paper_2112_07862_gb300", "csrc", f), "rb").read()
+                       for f in ("lobpcg.cu", "cheb.cu"))
         if d.get("source_sha256") != hashlib.sha256(src).hexdigest():
             return None
         return d.get("dram_bytes_per_launch")
@@ -192,11 +193,16 @@ def run_ours(a, dist):
     oo = mge.ops_opts(a.precision, stream=sptr)
     eo = mge.embed_opts(a.precision, v_on_device=True, stream=sptr)
     status = {"build": None, "embed": None}
+    phases = {"build_ms": [], "embed_ms": [], "eps_iters": []}
 
     def step():
         flush.zero_()
         h, s = mge.mge_build_graph_ops(ctx.h, g.n, rp_d, col_d, w_d, True, oo)
         lam, V, info, s2 = mge.mge_embed(ctx.h, h, a.K, a.tol, eo, V_d)
+        oi = mge.mge_ops_info(h)
+        phases["build_ms"].append(oi.build_ms)
+        phases["eps_iters"].append(oi.eps_iters)
+        phases["embed_ms"].append(info.solve_ms)
         mge.mge_ops_destroy(h)
         status["build"], status["embed"] = s, s2
         return lam, info
@@ -204,8 +210,8 @@ def run_ours(a, dist):
     for _ in range(a.warmup):
         step()
     torch.cuda.synchronize()
-    mge.mge_ctx_reset_stats(ctx.h)
-    mge.mge_ctx_set_timing(ctx.h, True)
+    for v in phases.values():
+        v.clear()
     clocks = ClockSampler(dist.local)
     clocks.start()
     dist.barrier()
@@ -221,9 +227,15 @@ def run_ours(a, dist):
     torch.cuda.synchronize()
     dist.barrier()
     clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    # per-launch SpMM times for the roofline: one more step with the library's event timing
+    # on (outside the timed region: the events around every SpMM launch cost time)
+    mge.mge_ctx_reset_stats(ctx.h)
+    mge.mge_ctx_set_timing(ctx.h, True)
+    step()
+    torch.cuda.synchronize()
     mge.mge_ctx_set_timing(ctx.h, False)
     st = mge.mge_ctx_stats(ctx.h)
-    ms = e0.elapsed_time(e1)
     ms_max = dist.max(ms)
     per_step = ms_max / a.steps
     value = dist.world * g.n * a.steps / (ms_max / 1e3)
@@ -269,10 +281,11 @@ def run_ours(a, dist):
         hbm, peak_src = 6800.0, "of fallback"
     achieved = (st.spmm_bytes / (st.spmm_ms / 1e3) / 1e9) if st.spmm_ms > 0 else None
     traffic = spmm_traffic_per_launch()
-    # k_spmm_w runs in two modes: A W_raw with the fused projection/normalisation of W (once per
-    # iteration) and the Chebyshev preconditioner steps on L + eps I (degree - 1 per
-    # iteration); achieved = algorithmic bytes of all timed launches / their summed event time
-    roofline = {"kernel": "k_spmm_w (fused A*W_raw, and the Chebyshev preconditioner steps on L + eps I)",
+    # the SpMMs of both solves: k_cheb, the Chebyshev preconditioner steps (degree - 1 per
+    # iteration, on L + eps I in the embedding and on Q in the eps solve), and k_spmm_w, the
+    # operator product with the fused projection/normalisation of W (once per iteration);
+    # achieved = algorithmic bytes of all timed launches / their summed event time
+    roofline = {"kernel": "k_cheb (Chebyshev preconditioner steps) and k_spmm_w (A W_raw, fused projection)",
                 "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": (achieved / hbm) if achieved else None, "peak_source": peak_src,
                 "traffic": traffic, "launches_timed": st.spmm_launches,
@@ -285,8 +298,11 @@ def run_ours(a, dist):
         "data": "synthetic: seeded swiss-roll points, exact symmetric kNN graph, Gaussian weights",
         "config": dict(workload(a), l2="flushed (256 MB write) before every step",
                        parallelism=f"replicas x{dist.world} (independent graphs, no collective)"),
-        "gpu_launches": int(st.kernel_launches),
+        "gpu_launches": int(st.kernel_launches) * a.steps,
         "lobpcg_iters_per_step": statistics.mean(iters),
+        "phases": {"build_ms": statistics.mean(phases["build_ms"][:a.steps]),
+                   "embed_ms": statistics.mean(phases["embed_ms"][:a.steps]),
+                   "eps_iters": statistics.mean(phases["eps_iters"][:a.steps])},
         "status": {"build": status["build"], "embed": status["embed"]},
         "roofline": roofline,
         "e2e": e2e,

@@ -105,7 +105,7 @@ typedef struct {
   double   mu_override;
   double   eps_tol;           /* backward-error tolerance of the eps solve (0 = default:
                                  1e-12 in FP64, 2e-7 in FP32/BF16)                          */
-  int      eps_guard;         /* extra LOBPCG columns for the eps solve (default 3)         */
+  int      eps_guard;         /* extra LOBPCG columns for the eps solve (default 7)         */
   int      eps_maxiter;       /* default 20000                                              */
   uint64_t seed;              /* seed of the eps solve's initial block                      */
   void*    stream;            /* cudaStream_t or NULL                                       */
@@ -210,13 +210,14 @@ typedef struct {
   int         v_on_device;    /* V is a device pointer                                      */
   void*       stream;         /* cudaStream_t or NULL                                       */
   int         precond_degree; /* LOBPCG preconditioner: the residual block R becomes
-                                 p(D^-1 A) D^-1 R, p the degree-d Chebyshev iteration for
-                                 A y = R on [beta / (2 d^2), beta], D = diag(A), beta the
-                                 Gershgorin bound of D^-1 A.  d = 1 is the Jacobi
-                                 preconditioner; each degree above 1 costs one SpMM per
-                                 iteration and cuts the iteration count about in proportion.
-                                 The paper leaves the preconditioner open.  0 = default 24;
-                                 at most 64.                                                */
+                                 p(D^-1 L') D^-1 R, p the degree-d Chebyshev iteration for
+                                 L' y = R on [beta / (2 d^2), beta], with L' = L + eps I (the
+                                 Laplacian of W shifted by eps, a sparser stand-in for A),
+                                 D = diag(L') and beta the Gershgorin bound of D^-1 L'.
+                                 d = 1 is the Jacobi preconditioner; each degree above 1
+                                 costs one SpMM of L' per iteration and cuts the iteration
+                                 count about in proportion.  The paper leaves the
+                                 preconditioner open.  0 = default 48; at most 64.          */
 } mge_embed_opts;
 
 typedef struct {

@@ -845,13 +845,15 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
       qop.shift = 0.0; qop.b = nullptr;
       qop.dinv = (o.precision == MGE_FP64) ? (const void*)ops->dinv_q.p : (const void*)ops->dinv_q32.p;
       qop.norm = ops->norm_q; qop.bmax = 1.0; qop.deflate = true; qop.beta = ops->beta_q;
-      qop.precond_degree = o.eps_precond_degree > 0 ? std::min(o.eps_precond_degree, 64) : kDefaultPrecondDegree;
+      qop.precond_degree = o.eps_precond_degree > 0 ? std::min(o.eps_precond_degree, 64) : kDefaultEpsPrecondDegree;
       if (ops->q_sl.built()) {
         qop.sl_slp = ops->q_sl.slp.p; qop.sl_perm = ops->q_sl.perm.p; qop.sl_col = ops->q_sl.col.p;
         qop.sl_val = (o.precision == MGE_FP64) ? (const void*)ops->q_sl.val.p : (const void*)ops->q_sl.val32.p;
         qop.sl_max_tile_slots = ops->q_sl.max_tile_slots;
       }
-      int guard = o.eps_guard > 0 ? o.eps_guard : 3;
+      // default block m = 8 (fewer iterations than m = 4 at about the same SpMM time), m = 4
+      // on graphs too small for it
+      int guard = o.eps_guard > 0 ? o.eps_guard : (n >= 2 * 8 ? 7 : 3);
       int m = round_block_width(1 + guard);
       if (m > n - 1) m = -1;
       double tol = o.eps_tol > 0 ? o.eps_tol : (o.precision == MGE_FP64 ? 1e-12 : 2e-7);
