@@ -940,6 +940,16 @@ __global__ void k_write_v(int64_t n, int M, int K, const T* X, const unsigned lo
 
 inline unsigned gridn(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// Last node of the device-side iteration loop: run another pass while the solve is running
+// (and below the iteration limit, a bound that does not rely on the solver's own check).
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, State* st, int maxiter) {
+  if (threadIdx.x == 0) {
+    st->loops += 1;
+    const bool more = st->done == DONE_RUNNING && st->iter < maxiter;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+  }
+}
+
 // =======================================================================================
 // host driver
 // =======================================================================================
@@ -1264,14 +1274,9 @@ struct Solver {
     return MGE_OK;
   }
 
-  mge_status run(int check_every, bool use_graph, uint64_t seed, const double* x0, int x0_cols,
-                 double* V_out, LobResult* res) {
-    cudaEvent_t e0, e1;
-    MGE_CUDA(ctx, cudaEventCreate(&e0));
-    MGE_CUDA(ctx, cudaEventCreate(&e1));
-    MGE_CUDA(ctx, cudaEventRecord(e0, st));
-    const bool timed = ctx->timing;
-    // --- init: W_raw = X0, normalise, Rayleigh-Ritz on span(W) ---
+  // the initial block (W_raw = X0, normalised, Rayleigh-Ritz on span(W)) and the first
+  // iteration, S = [X W]
+  mge_status prologue(uint64_t seed, const double* x0, int x0_cols, bool timed) {
     k_init_block<T><<<gridn(n * M, 256), 256, 0, st>>>(n, M, seed, x0, x0_cols, op.row_order, Wr.p);
     MGE_LAUNCHED(ctx, 1);
     wsrc = Wr.p;
@@ -1284,7 +1289,6 @@ struct Solver {
     MGE_TRY(launch_cheb(timed));
     launch_gram_w(true, false);
     launch_wprep_(true, false, true);
-    // --- first iteration: S = [X W] ---
     MGE_TRY(launch_spmm(true, false, timed));
     launch_gram_s(2);
     launch_rr_(2, M);
@@ -1292,11 +1296,75 @@ struct Solver {
     MGE_TRY(launch_cheb(timed));
     launch_gram_w(true, true);
     launch_wprep_(true, true, true);
+    return MGE_OK;
+  }
+
+  mge_status run(int check_every, bool use_graph, uint64_t seed, const double* x0, int x0_cols,
+                 double* V_out, LobResult* res) {
+    cudaEvent_t e0, e1;
+    MGE_CUDA(ctx, cudaEventCreate(&e0));
+    MGE_CUDA(ctx, cudaEventCreate(&e1));
+    MGE_CUDA(ctx, cudaEventRecord(e0, st));
+    const bool timed = ctx->timing;
+    bool graph_ok = use_graph;
+    if (graph_ok) {
+      cudaStreamCaptureStatus cs;
+      MGE_CUDA(ctx, cudaStreamIsCapturing(st, &cs));
+      if (cs != cudaStreamCaptureStatusNone) graph_ok = false;
+    }
+    // Without per-launch events (which a graph loop cannot hold) the whole solve is one graph:
+    // the prologue, then a conditional (while) node whose body is one iteration and ends with
+    // a kernel that decides on the device whether to run another pass.
+    const bool loop_graph = graph_ok && !timed;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    uint64_t per_pass = 0;
+    if (loop_graph) {
+      cudaGraph_t pro = nullptr;
+      MGE_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      mge_status cap = prologue(seed, x0, x0_cols, false);
+      cudaError_t ce = cudaStreamEndCapture(st, &pro);
+      if (cap != MGE_OK) { if (pro) cudaGraphDestroy(pro); return cap; }
+      if (ce != cudaSuccess) { set_error(ctx, "graph capture failed: %s", cudaGetErrorString(ce)); return MGE_EDEVICE; }
+      MGE_CUDA(ctx, cudaGraphCreate(&graph, 0));
+      cudaGraphNode_t npro = nullptr, nloop = nullptr;
+      cudaError_t e1c = cudaGraphAddChildGraphNode(&npro, graph, nullptr, 0, pro);
+      cudaGraphDestroy(pro);                      // the node holds its own copy
+      MGE_CUDA(ctx, e1c);
+      cudaGraphConditionalHandle h;
+      MGE_CUDA(ctx, cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      MGE_CUDA(ctx, cudaGraphAddNode(&nloop, graph, &npro, nullptr, 1, &cp));
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      MGE_CUDA(ctx, cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      const uint64_t before = ctx->kernel_launches;
+      cap = iteration(3, false);
+      if (cap == MGE_OK) {
+        k_loop_cond<<<1, 32, 0, st>>>(h, state, maxiter);
+        MGE_LAUNCHED(ctx, 1);
+      }
+      cudaGraph_t body_out = nullptr;
+      ce = cudaStreamEndCapture(st, &body_out);
+      per_pass = ctx->kernel_launches - before;
+      ctx->kernel_launches = before;
+      if (cap != MGE_OK) { cudaGraphDestroy(graph); return cap; }
+      if (ce != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        set_error(ctx, "graph capture failed: %s", cudaGetErrorString(ce));
+        return MGE_EDEVICE;
+      }
+      MGE_CUDA(ctx, cudaGraphInstantiate(&gexec, graph, 0));
+      MGE_CUDA(ctx, cudaGraphLaunch(gexec, st));
+    } else {
+      MGE_TRY(prologue(seed, x0, x0_cols, timed));
+    }
     MGE_CUDA(ctx, cudaGetLastError());
     State* hst = nullptr;
     MGE_CUDA(ctx, cudaMallocHost(&hst, sizeof(State)));
-    cudaGraphExec_t gexec = nullptr;
-    cudaGraph_t graph = nullptr;
     mge_status status = MGE_OK;
     if (check_every < 1) check_every = 1;
     auto finish_timing = [&]() -> mge_status {
@@ -1315,13 +1383,7 @@ struct Solver {
       return MGE_OK;
     };
     MGE_TRY(finish_timing());
-    bool graph_ok = use_graph;
-    if (graph_ok) {
-      cudaStreamCaptureStatus cs;
-      MGE_CUDA(ctx, cudaStreamIsCapturing(st, &cs));
-      if (cs != cudaStreamCaptureStatusNone) graph_ok = false;
-    }
-    if (graph_ok) {
+    if (graph_ok && !loop_graph) {
       MGE_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       uint64_t before = ctx->kernel_launches;
       mge_status cap = MGE_OK;
@@ -1337,6 +1399,10 @@ struct Solver {
     for (;;) {
       MGE_CUDA(ctx, cudaMemcpyAsync(hst, state, sizeof(State), cudaMemcpyDeviceToHost, st));
       MGE_CUDA(ctx, cudaStreamSynchronize(st));
+      if (loop_graph) {
+        ctx->kernel_launches += per_pass * (uint64_t)hst->loops;
+        break;
+      }
       if (hst->done != DONE_RUNNING) break;
       if (graph_ok) {
         if (timed) {
@@ -1360,7 +1426,7 @@ struct Solver {
       status = (mge_status)hst->err;
       set_error(ctx, "LOBPCG stopped at iteration %d: %s (stage %d, kept %d)", hst->iter,
                 mge_strerror(status), hst->bad_stage, hst->kept);
-    } else if (hst->done == DONE_MAXITER) {
+    } else if (hst->done == DONE_MAXITER || hst->done == DONE_RUNNING) {
       status = MGE_ENOTCONVERGED;
     }
     if (getenv("MGE_PHASES")) {

@@ -26,7 +26,8 @@ struct State {
   int drops;
   int kept;
   int bad_stage;     // 1: Rayleigh-Ritz input, 2: residual / Ritz values, 3: W Gram, 4: RR output
-  int pad[2];
+  int loops;         // passes of the device-side iteration loop (graph mode)
+  int pad1;
   long long rr_clk[16];     // clock64 deltas at the phase boundaries of the last Rayleigh-Ritz
   long long wp_clk[8];      // and of the last wprep (diagnostics)
   double lambda[MAXM];
