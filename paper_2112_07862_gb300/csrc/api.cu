@@ -51,6 +51,30 @@ void dev_free(Ctx* ctx, void* p, size_t bytes) {
   if (ctx) ctx->in_use -= bytes;
 }
 
+mge_status dev_alloc_async(Ctx* ctx, void** p, size_t bytes, cudaStream_t st) {
+  if (!ctx->pool) return dev_alloc(ctx, p, bytes);
+  if (ctx->budget && ctx->in_use.load() + bytes > ctx->budget) {
+    set_error(ctx, "HBM budget exceeded: %zu in use + %zu requested > %zu", ctx->in_use.load(), bytes,
+              ctx->budget);
+    return MGE_ENOMEM;
+  }
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, st);
+  if (e != cudaSuccess) {
+    set_error(ctx, "cudaMallocFromPoolAsync(%zu): %s", bytes, cudaGetErrorString(e));
+    *p = nullptr;
+    return MGE_ENOMEM;
+  }
+  ctx->in_use += bytes;
+  return MGE_OK;
+}
+
+void dev_free_async(Ctx* ctx, void* p, size_t bytes, cudaStream_t st) {
+  if (!p) return;
+  if (!ctx || !ctx->pool) { dev_free(ctx, p, bytes); return; }
+  cudaFreeAsync(p, st);
+  ctx->in_use -= bytes;
+}
+
 static cudaStream_t pick_stream(Ctx* ctx, void* s) {
   return s ? static_cast<cudaStream_t>(s) : ctx->stream;
 }
@@ -95,6 +119,20 @@ mge_status mge_create(int device, size_t hbm_budget_bytes, mge_ctx** out) {
   ctx->num_sms = prop.multiProcessorCount;
   ctx->self = c;
   if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return MGE_EDEVICE; }
+  {
+    // the scratch pool keeps what it is given back (release threshold: never)
+    cudaMemPoolProps pp = {};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = device;
+    if (cudaMemPoolCreate(&ctx->pool, &pp) == cudaSuccess) {
+      uint64_t keep = ~0ull;
+      cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      ctx->pool = nullptr;
+      cudaGetLastError();
+    }
+  }
   *out = c;
   return MGE_OK;
 }
@@ -102,7 +140,15 @@ mge_status mge_create(int device, size_t hbm_budget_bytes, mge_ctx** out) {
 // The context's host object lives until the last ops handle built from it is destroyed, so
 // an ops handle may outlive mge_destroy (its device memory is released by mge_ops_destroy).
 static void ctx_release(Ctx* ctx) {
-  if (--ctx->refs == 0) delete static_cast<mge_ctx*>(ctx->self);
+  if (--ctx->refs == 0) {
+    cudaSetDevice(ctx->device);
+    if (ctx->pool) {
+      cudaDeviceSynchronize();          // every scratch free has completed
+      cudaMemPoolDestroy(ctx->pool);
+    }
+    for (void* h : ctx->state_host) cudaFreeHost(h);
+    delete static_cast<mge_ctx*>(ctx->self);
+  }
 }
 
 mge_status mge_destroy(mge_ctx* c) {
@@ -423,7 +469,7 @@ mge_status mge_embed(mge_ctx* c, const mge_ops* o, int K, double tol, const mge_
     x0c = std::min(e.x0_cols, m);
     if (e.x0_on_device) x0 = e.x0;
     else {
-      MGE_TRY(x0d.alloc(ctx, (size_t)op.n * x0c));
+      MGE_TRY(x0d.scratch(ctx, (size_t)op.n * x0c, st));
       MGE_CUDA(ctx, cudaMemcpyAsync(x0d.p, e.x0, (size_t)op.n * x0c * sizeof(double), cudaMemcpyHostToDevice, st));
       x0 = x0d.p;
     }
@@ -432,7 +478,7 @@ mge_status mge_embed(mge_ctx* c, const mge_ops* o, int K, double tol, const mge_
   double* vout = nullptr;
   if (V) {
     if (e.v_on_device) vout = static_cast<double*>(V);
-    else { MGE_TRY(vd.alloc(ctx, (size_t)op.n * K)); vout = vd.p; }
+    else { MGE_TRY(vd.scratch(ctx, (size_t)op.n * K, st)); vout = vd.p; }
   }
   LobResult r;
   l.precond_degree = e.precond_degree > 0 ? std::min(e.precond_degree, 64) : kDefaultPrecondDegree;

@@ -136,13 +136,12 @@ mge_status exclusive_scan(Ctx* ctx, cudaStream_t st, const int64_t* in, int64_t 
   }
   int64_t nb = (n + kScanBlock - 1) / kScanBlock;
   DevBuf<int64_t> part;
-  MGE_TRY(part.alloc(ctx, nb));
+  MGE_TRY(part.scratch(ctx, nb, st));
   k_scan_partial<<<(unsigned)nb, kScanBlock, 0, st>>>(in, n, part.p);
   k_scan_top<<<1, kScanBlock, 0, st>>>(part.p, nb);
   k_scan_final<<<(unsigned)nb, kScanBlock, 0, st>>>(in, n, part.p, out);
   MGE_LAUNCHED(ctx, 3);
   MGE_CUDA(ctx, cudaGetLastError());
-  MGE_CUDA(ctx, cudaStreamSynchronize(st));  // `part` is freed on return
   return MGE_OK;
 }
 
@@ -603,8 +602,8 @@ mge_status build_sliced(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* rp,
   DevBuf<unsigned long long> mx;
   MGE_TRY(slp.alloc(ctx, ns + 4));
   MGE_TRY(perm.alloc(ctx, ntiles * kSliceTileRows));
-  MGE_TRY(cnt.alloc(ctx, ns));
-  MGE_TRY(mx.alloc(ctx, 1));
+  MGE_TRY(cnt.scratch(ctx, ns, st));
+  MGE_TRY(mx.scratch(ctx, 1, st));
   MGE_CUDA(ctx, cudaMemsetAsync(mx.p, 0, sizeof(unsigned long long), st));
   k_slice_rank<<<(unsigned)ntiles, kSliceTileRows, 0, st>>>(n, rp, perm.p, cnt.p, mx.p);
   MGE_LAUNCHED(ctx, 1);
@@ -694,8 +693,8 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
   const double* w = ops->w_val.p;
 
   // small device scalars: [err, big_count, ncomp] and doubles [den_max, normq, norma, bmax, sumlog]
-  DevBuf<unsigned> d_err;  MGE_TRY(d_err.alloc(ctx, 4));
-  DevBuf<double> d_sc;     MGE_TRY(d_sc.alloc(ctx, 8));
+  DevBuf<unsigned> d_err;  MGE_TRY(d_err.scratch(ctx, 4, st));
+  DevBuf<double> d_sc;     MGE_TRY(d_sc.scratch(ctx, 8, st));
   MGE_CUDA(ctx, cudaMemsetAsync(d_err.p, 0, 4 * sizeof(unsigned), st));
   MGE_CUDA(ctx, cudaMemsetAsync(d_sc.p, 0, 8 * sizeof(double), st));
   unsigned* err = d_err.p;
@@ -747,9 +746,9 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
   // --- two-hop sets ---
   DevBuf<int64_t> cnt, U;
   DevBuf<int32_t> big_list;
-  MGE_TRY(cnt.alloc(ctx, n));
-  MGE_TRY(U.alloc(ctx, n + 1));
-  MGE_TRY(big_list.alloc(ctx, n));
+  MGE_TRY(cnt.scratch(ctx, n, st));
+  MGE_TRY(U.scratch(ctx, n + 1, st));
+  MGE_TRY(big_list.scratch(ctx, n, st));
   k_cand_count<<<grid_for(n, B), B, 0, st>>>(n, rp, col, cnt.p, big_list.p, big_count);
   MGE_LAUNCHED(ctx, 1);
   MGE_TRY(exclusive_scan(ctx, st, cnt.p, n, U.p));
@@ -759,7 +758,7 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
   MGE_CUDA(ctx, cudaMemcpyAsync(&h_big, big_count, sizeof(int), cudaMemcpyDeviceToHost, st));
   MGE_CUDA(ctx, cudaStreamSynchronize(st));
   DevBuf<int32_t> tlist;
-  MGE_TRY(tlist.alloc(ctx, std::max<int64_t>(total_cand, 1)));
+  MGE_TRY(tlist.scratch(ctx, std::max<int64_t>(total_cand, 1), st));
   MGE_TRY(ops->T.alloc(ctx, n));
   {
     int blocks = std::min<int64_t>(grid_for(n, kWarpsPerBlock), (int64_t)ctx->num_sms * 16);
@@ -769,7 +768,7 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
   if (h_big > 0) {
     int nb = std::min(h_big, 64);
     DevBuf<unsigned> bitmaps;
-    MGE_TRY(bitmaps.alloc(ctx, (size_t)nb * ((n + 31) / 32)));
+    MGE_TRY(bitmaps.scratch(ctx, (size_t)nb * ((n + 31) / 32), st));
     k_twohop_big<<<nb, 1024, 0, st>>>(n, rp, col, big_list.p, h_big, U.p, bitmaps.p, tlist.p, ops->T.p);
     MGE_LAUNCHED(ctx, 1);
     MGE_CUDA(ctx, cudaGetLastError());
@@ -779,8 +778,8 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
 
   // --- structures of Q and A ---
   DevBuf<int64_t> qcnt, acnt;
-  MGE_TRY(qcnt.alloc(ctx, n));
-  MGE_TRY(acnt.alloc(ctx, n));
+  MGE_TRY(qcnt.scratch(ctx, n, st));
+  MGE_TRY(acnt.scratch(ctx, n, st));
   // CSR arrays carry a few zeroed elements past their ends: the LOBPCG SpMM copies row
   // pointers, column indices and values in tiles whose byte counts are rounded up to 16
   MGE_TRY(ops->q_ptr.alloc(ctx, n + 2));
@@ -816,7 +815,7 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
   // --- components of the two-hop graph (eps = 0 when more than one) ---
   {
     DevBuf<int32_t> parent;
-    MGE_TRY(parent.alloc(ctx, n));
+    MGE_TRY(parent.scratch(ctx, n, st));
     k_cc_init<<<grid_for(n, B), B, 0, st>>>(n, parent.p);
     k_cc_union<<<grid_for(n, B), B, 0, st>>>(n, ops->T.p, U.p, tlist.p, parent.p, err);
     k_cc_count<<<grid_for(n, B), B, 0, st>>>(n, parent.p, ncomp);
@@ -898,8 +897,8 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
   MGE_TRY(ops->dinv_a32.alloc(ctx, n + 4));
   MGE_CUDA(ctx, cudaMemsetAsync(ops->dinv_a32.p + n, 0, 4 * sizeof(float), st));
   DevBuf<double> r, logr;
-  MGE_TRY(r.alloc(ctx, n));
-  MGE_TRY(logr.alloc(ctx, n));
+  MGE_TRY(r.scratch(ctx, n, st));
+  MGE_TRY(logr.scratch(ctx, n, st));
   k_fill_a<<<grid_for(n, B), B, 0, st>>>(n, rp, col, w, ops->T.p, U.p, tlist.p, ops->q_ptr.p,
                                           ops->q_val.p, ops->q_col.p, ops->mu, ops->eps, ops->a_ptr.p,
                                           ops->a_col.p, ops->a_val.p, r.p, logr.p, err);
@@ -907,7 +906,7 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
   {
     const int np = 256;
     DevBuf<double> part;
-    MGE_TRY(part.alloc(ctx, np));
+    MGE_TRY(part.scratch(ctx, np, st));
     k_sum_partial<<<np, 256, 0, st>>>(logr.p, n, part.p);
     k_sum_final<<<1, 256, 0, st>>>(part.p, np, sumlog);
     MGE_LAUNCHED(ctx, 2);

@@ -990,14 +990,14 @@ struct Solver {
 
   mge_status setup() {
     size_t blk = (size_t)n * M;
-    MGE_TRY(X.alloc(ctx, blk)); MGE_TRY(AX.alloc(ctx, blk));
-    MGE_TRY(P.alloc(ctx, blk)); MGE_TRY(AP.alloc(ctx, blk));
-    MGE_TRY(W.alloc(ctx, blk)); MGE_TRY(AW.alloc(ctx, blk));
-    MGE_TRY(Wr.alloc(ctx, blk));
+    MGE_TRY(X.scratch(ctx, blk, st)); MGE_TRY(AX.scratch(ctx, blk, st));
+    MGE_TRY(P.scratch(ctx, blk, st)); MGE_TRY(AP.scratch(ctx, blk, st));
+    MGE_TRY(W.scratch(ctx, blk, st)); MGE_TRY(AW.scratch(ctx, blk, st));
+    MGE_TRY(Wr.scratch(ctx, blk, st));
     wsrc = Wr.p;
     cheb_deg = std::max(1, std::min(op.precond_degree, 64));
     if (cheb_deg > 1) {
-      MGE_TRY(Yc0.alloc(ctx, blk)); MGE_TRY(Yc1.alloc(ctx, blk)); MGE_TRY(Dc.alloc(ctx, blk));
+      MGE_TRY(Yc0.scratch(ctx, blk, st)); MGE_TRY(Yc1.scratch(ctx, blk, st)); MGE_TRY(Dc.scratch(ctx, blk, st));
       // Chebyshev iteration for A y = r on [alpha, beta] of the spectrum of D^-1 A: beta is the
       // Gershgorin bound, alpha = beta / (2 d^2) so that the polynomial reduces the condition
       // number of the preconditioned block by about d^2
@@ -1011,7 +1011,7 @@ struct Solver {
     size_t off_t = ((sizeof(Small) + 255) / 256) * 256;
     size_t off_s = off_t + ((sizeof(SmallT<T>) + 255) / 256) * 256;
     size_t bytes = off_s + sizeof(State);
-    MGE_TRY(small.alloc(ctx, bytes));
+    MGE_TRY(small.scratch(ctx, bytes, st));
     MGE_CUDA(ctx, cudaMemsetAsync(small.p, 0, bytes, st));
     sm = reinterpret_cast<Small*>(small.p);
     smt = reinterpret_cast<SmallT<T>*>(small.p + off_t);
@@ -1364,7 +1364,15 @@ struct Solver {
     }
     MGE_CUDA(ctx, cudaGetLastError());
     State* hst = nullptr;
-    MGE_CUDA(ctx, cudaMallocHost(&hst, sizeof(State)));
+    {
+      // a pinned status buffer from the context's free list (pinned allocation is slow)
+      std::lock_guard<std::mutex> lock(ctx->state_mu);
+      if (!ctx->state_host.empty()) {
+        hst = static_cast<State*>(ctx->state_host.back());
+        ctx->state_host.pop_back();
+      }
+    }
+    if (!hst) MGE_CUDA(ctx, cudaMallocHost(&hst, sizeof(State)));
     mge_status status = MGE_OK;
     if (check_every < 1) check_every = 1;
     auto finish_timing = [&]() -> mge_status {
@@ -1455,7 +1463,10 @@ struct Solver {
     res->ms = ms;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFreeHost(hst);
+    {
+      std::lock_guard<std::mutex> lock(ctx->state_mu);
+      ctx->state_host.push_back(hst);
+    }
     res->status = status;
     return status;
   }
@@ -1577,7 +1588,7 @@ mge_status spmm_apply(Ctx* ctx, cudaStream_t st, const LobOp& op, int precision,
   const size_t elem = precision == MGE_FP64 ? sizeof(double) : sizeof(float);
   const int vec = (int)((size_t)m * elem / 16);
   DevBuf<uint4> xi;
-  MGE_TRY(xi.alloc(ctx, (size_t)op.n * vec));
+  MGE_TRY(xi.scratch(ctx, (size_t)op.n * vec, st));
   k_gather_rows<<<lob::gridn(op.n * vec, 256), 256, 0, st>>>(op.n, vec, op.row_order, static_cast<const uint4*>(X), xi.p);
   MGE_LAUNCHED(ctx, 1);
   MGE_CUDA(ctx, cudaGetLastError());

@@ -60,6 +60,11 @@ struct Ctx {
   std::string last_error;
   std::mutex err_mu;
   int num_sms = 0;
+  // stream-ordered pool for the scratch of one call (freed memory stays in the pool, so a
+  // repeated call neither allocates from the driver nor synchronises the device)
+  cudaMemPool_t pool = nullptr;
+  std::vector<void*> state_host;   // pinned host copies of solve status words (reused)
+  std::mutex state_mu;
   void* serve = nullptr;           // serving state (serve.cu)
   void* self = nullptr;            // the owning mge_ctx*
   std::atomic<int> refs{1};        // the context itself plus one per live ops handle
@@ -68,12 +73,21 @@ struct Ctx {
 
 mge_status dev_alloc(Ctx* ctx, void** p, size_t bytes);
 void dev_free(Ctx* ctx, void* p, size_t bytes);
+// scratch ordered on stream st: usable by work on st after this call, returned to the
+// context's pool by work on st (the caller uses it on st only)
+mge_status dev_alloc_async(Ctx* ctx, void** p, size_t bytes, cudaStream_t st);
+void dev_free_async(Ctx* ctx, void* p, size_t bytes, cudaStream_t st);
 
+// Device array owned by the library: alloc() for memory that outlives the call (the
+// operators; cudaMalloc), scratch() for memory used by one call on one stream (the
+// context's stream-ordered pool).
 template <typename T>
 struct DevBuf {
   T* p = nullptr;
   size_t n = 0;
   Ctx* ctx = nullptr;
+  bool pooled = false;
+  cudaStream_t st = nullptr;
   mge_status alloc(Ctx* c, size_t count) {
     release();
     ctx = c;
@@ -85,10 +99,28 @@ struct DevBuf {
     p = static_cast<T*>(q);
     return MGE_OK;
   }
+  mge_status scratch(Ctx* c, size_t count, cudaStream_t stream) {
+    release();
+    ctx = c;
+    n = count;
+    if (count == 0) return MGE_OK;
+    void* q = nullptr;
+    mge_status s = dev_alloc_async(c, &q, count * sizeof(T), stream);
+    if (s != MGE_OK) { n = 0; return s; }
+    p = static_cast<T*>(q);
+    pooled = true;
+    st = stream;
+    return MGE_OK;
+  }
   void release() {
-    if (p) dev_free(ctx, p, n * sizeof(T));
+    if (p) {
+      if (pooled) dev_free_async(ctx, p, n * sizeof(T), st);
+      else dev_free(ctx, p, n * sizeof(T));
+    }
     p = nullptr;
     n = 0;
+    pooled = false;
+    st = nullptr;
   }
   ~DevBuf() { release(); }
   DevBuf() = default;

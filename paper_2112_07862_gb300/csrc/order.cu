@@ -175,8 +175,8 @@ mge_status locality_order(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* r
   // --- cells: multi-source BFS to the fixed point ---
   DevBuf<uint64_t> s;
   DevBuf<int> changed;
-  MGE_TRY(s.alloc(ctx, n));
-  MGE_TRY(changed.alloc(ctx, 1));
+  MGE_TRY(s.scratch(ctx, n, st));
+  MGE_TRY(changed.scratch(ctx, 1, st));
   k_cell_init<<<blocks_for(n, B), B, 0, st>>>(n, s.p);
   MGE_LAUNCHED(ctx, 1);
   int sweeps = 0;
@@ -193,8 +193,8 @@ mge_status locality_order(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* r
   }
   // --- keys: cell index (cells numbered by their seed), then distance ---
   DevBuf<int64_t> head, cell_of;
-  MGE_TRY(head.alloc(ctx, n));
-  MGE_TRY(cell_of.alloc(ctx, n + 1));
+  MGE_TRY(head.scratch(ctx, n, st));
+  MGE_TRY(cell_of.scratch(ctx, n + 1, st));
   k_cell_heads<<<blocks_for(n, B), B, 0, st>>>(n, s.p, head.p);
   MGE_LAUNCHED(ctx, 1);
   MGE_TRY(scan_exclusive(ctx, st, head.p, n, cell_of.p));
@@ -203,10 +203,10 @@ mge_status locality_order(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* r
   MGE_CUDA(ctx, cudaStreamSynchronize(st));
   DevBuf<uint64_t> key0, key1;
   DevBuf<int32_t> val0, val1;
-  MGE_TRY(key0.alloc(ctx, n));
-  MGE_TRY(key1.alloc(ctx, n));
-  MGE_TRY(val0.alloc(ctx, n));
-  MGE_TRY(val1.alloc(ctx, n));
+  MGE_TRY(key0.scratch(ctx, n, st));
+  MGE_TRY(key1.scratch(ctx, n, st));
+  MGE_TRY(val0.scratch(ctx, n, st));
+  MGE_TRY(val1.scratch(ctx, n, st));
   k_cell_keys<<<blocks_for(n, B), B, 0, st>>>(n, s.p, cell_of.p, key0.p, val0.p);
   MGE_LAUNCHED(ctx, 1);
   // --- stable radix sort over the key's significant bits ---
@@ -214,8 +214,8 @@ mge_status locality_order(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* r
   while (bits < 64 && (((uint64_t)std::max<int64_t>(ncells - 1, 0) << 8) >> bits) != 0) ++bits;
   const int64_t nb = (n + kSortBlock - 1) / kSortBlock;
   DevBuf<int64_t> hist, off;
-  MGE_TRY(hist.alloc(ctx, 256 * nb));
-  MGE_TRY(off.alloc(ctx, 256 * nb + 1));
+  MGE_TRY(hist.scratch(ctx, 256 * nb, st));
+  MGE_TRY(off.scratch(ctx, 256 * nb + 1, st));
   uint64_t* kin = key0.p; uint64_t* kout = key1.p;
   int32_t* vin = val0.p; int32_t* vout = val1.p;
   for (int shift = 0; shift < bits; shift += 8) {
@@ -234,7 +234,7 @@ mge_status locality_order(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* r
   MGE_LAUNCHED(ctx, 1);
   // --- W in the new numbering (same padding as the input copy) ---
   DevBuf<int64_t> len;
-  MGE_TRY(len.alloc(ctx, n));
+  MGE_TRY(len.scratch(ctx, n, st));
   MGE_TRY(rp_out->alloc(ctx, n + 2));
   MGE_TRY(col_out->alloc(ctx, nnz + 4));
   MGE_TRY(w_out->alloc(ctx, nnz));
@@ -246,7 +246,6 @@ mge_status locality_order(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* r
   k_perm_fill<<<blocks_for(n, B), B, 0, st>>>(n, rp, col, w, order->p, rank->p, rp_out->p, col_out->p, w_out->p);
   MGE_LAUNCHED(ctx, 1);
   MGE_CUDA(ctx, cudaGetLastError());
-  MGE_CUDA(ctx, cudaStreamSynchronize(st));    // the scratch buffers are freed on return
   return MGE_OK;
 }
 
