@@ -51,6 +51,11 @@ void dev_free(Ctx* ctx, void* p, size_t bytes) {
   if (ctx) ctx->in_use -= bytes;
 }
 
+PersistentPool& persistent_pool() {
+  static thread_local PersistentPool p;
+  return p;
+}
+
 mge_status dev_alloc_async(Ctx* ctx, void** p, size_t bytes, cudaStream_t st) {
   if (!ctx->pool) return dev_alloc(ctx, p, bytes);
   if (ctx->budget && ctx->in_use.load() + bytes > ctx->budget) {
@@ -221,6 +226,10 @@ mge_status mge_ops_destroy(mge_ops* o) {
   if (!o) return MGE_EINVAL;
   Ctx* ctx = o->impl.ctx;
   if (ctx) cudaSetDevice(ctx->device);
+  // the arrays may be in use on any stream: wait for the device, then return the pooled ones
+  // on the default stream (the stream of the build may be gone)
+  cudaDeviceSynchronize();
+  o->impl.each_buffer([](auto& b) { if (b.pooled) b.st = nullptr; });
   delete o;
   if (ctx) ctx_release(ctx);
   return MGE_OK;

@@ -630,8 +630,8 @@ mge_status build_sliced(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* rp,
   out->ntiles = ntiles;
   out->slots = slots;
   out->max_tile_slots = (int64_t)h_mx;
-  std::swap(out->slp.p, slp.p); std::swap(out->slp.n, slp.n); out->slp.ctx = ctx;
-  std::swap(out->perm.p, perm.p); std::swap(out->perm.n, perm.n); out->perm.ctx = ctx;
+  out->slp.swap(slp);
+  out->perm.swap(perm);
   return MGE_OK;
 }
 
@@ -648,6 +648,8 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
                                 const int32_t* col_in, const double* w_in, int on_device,
                                 const mge_ops_opts* opts, Ops* ops) {
   if (n < 1) { set_error(ctx, "n must be >= 1"); return MGE_EINVAL; }
+  // the handle's arrays come from the context's pool, ordered on this stream
+  PersistentPoolScope pool_scope(st);
   if (!rp_in || !col_in || !w_in) { set_error(ctx, "null CSR pointer"); return MGE_EINVAL; }
   mge_ops_opts o{};
   o.precision = MGE_FP32;
@@ -735,9 +737,9 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
     DevBuf<double> w2;
     MGE_TRY(locality_order(ctx, st, n, ops->w_ptr.p, ops->w_col.p, ops->w_val.p, nnz, &ops->order, &ops->rank,
                            &rp2, &col2, &w2));
-    std::swap(ops->w_ptr.p, rp2.p); std::swap(ops->w_ptr.n, rp2.n);
-    std::swap(ops->w_col.p, col2.p); std::swap(ops->w_col.n, col2.n);
-    std::swap(ops->w_val.p, w2.p); std::swap(ops->w_val.n, w2.n);
+    ops->w_ptr.swap(rp2);
+    ops->w_col.swap(col2);
+    ops->w_val.swap(w2);
     rp = ops->w_ptr.p;
     col = ops->w_col.p;
     w = ops->w_val.p;

@@ -9,6 +9,7 @@
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/mge.h"
@@ -77,6 +78,18 @@ void dev_free(Ctx* ctx, void* p, size_t bytes);
 // context's pool by work on st (the caller uses it on st only)
 mge_status dev_alloc_async(Ctx* ctx, void** p, size_t bytes, cudaStream_t st);
 void dev_free_async(Ctx* ctx, void* p, size_t bytes, cudaStream_t st);
+// While set (the operator build), alloc() also draws from the pool, ordered on this stream;
+// such arrays are freed by mge_ops_destroy after a device synchronisation.
+struct PersistentPool {
+  bool on = false;
+  cudaStream_t st = nullptr;
+};
+PersistentPool& persistent_pool();
+struct PersistentPoolScope {
+  PersistentPool prev;
+  explicit PersistentPoolScope(cudaStream_t s) : prev(persistent_pool()) { persistent_pool() = PersistentPool{true, s}; }
+  ~PersistentPoolScope() { persistent_pool() = prev; }
+};
 
 // Device array owned by the library: alloc() for memory that outlives the call (the
 // operators; cudaMalloc), scratch() for memory used by one call on one stream (the
@@ -89,6 +102,7 @@ struct DevBuf {
   bool pooled = false;
   cudaStream_t st = nullptr;
   mge_status alloc(Ctx* c, size_t count) {
+    if (c && c->pool && persistent_pool().on) return scratch(c, count, persistent_pool().st);
     release();
     ctx = c;
     n = count;
@@ -121,6 +135,11 @@ struct DevBuf {
     n = 0;
     pooled = false;
     st = nullptr;
+  }
+  // exchange the arrays (and how each is to be freed) of two buffers
+  void swap(DevBuf& o) {
+    std::swap(p, o.p); std::swap(n, o.n); std::swap(ctx, o.ctx);
+    std::swap(pooled, o.pooled); std::swap(st, o.st);
   }
   ~DevBuf() { release(); }
   DevBuf() = default;
@@ -183,6 +202,15 @@ struct Ops {
   double beta_a = 2, beta_q = 2;            // Gershgorin bounds of the spectra of D^-1 A, D^-1 Q
   int degenerate = 0, ncomp = 1, eps_iters = 0;
   double eps_resid = 0, build_ms = 0;
+  // every device array of the handle
+  template <typename F>
+  void each_buffer(F f) {
+    f(order); f(rank); f(w_ptr); f(w_col); f(w_val); f(T);
+    f(q_ptr); f(q_col); f(q_val); f(a_ptr); f(a_col); f(a_val); f(q_val32); f(a_val32);
+    f(b); f(dinv_a); f(dinv_q); f(b32); f(dinv_a32); f(dinv_q32);
+    f(l_val); f(l_dinv); f(l_val32); f(l_dinv32);
+    for (Sliced* sl : {&q_sl, &l_sl}) { f(sl->slp); f(sl->perm); f(sl->col); f(sl->val); f(sl->val32); }
+  }
 };
 
 // ---------------------------------------------------------------------------------------
