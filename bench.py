@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--cpu-sample-n", type=int, default=10_000)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=32)
+    p.add_argument("--no-serving", action="store_true")
     return p.parse_args()
 
 
@@ -295,7 +297,7 @@ def run_ours(a, dist):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if a.precision == "fp32" else a.precision.replace("fp", "f"),
-        "data": "synthetic: seeded swiss-roll points, exact symmetric kNN graph, Gaussian weights",
+        "data": f"synthetic: seeded {a.shape.replace('_', '-')} points, exact symmetric kNN graph, Gaussian weights",
         "config": dict(workload(a), l2="flushed (256 MB write) before every step",
                        parallelism=f"replicas x{dist.world} (independent graphs, no collective)"),
         "gpu_launches": int(st.kernel_launches) * a.steps,
@@ -310,6 +312,70 @@ def run_ours(a, dist):
     }
     ctx.close()
     return res
+
+
+# ---------------------------------------------------------------------------------------
+# the serving form: Poisson arrivals through mge_submit / mge_poll
+# ---------------------------------------------------------------------------------------
+def run_serving(a):
+    """Requests of uneven size arrive as a Poisson stream (200 req/s, seed 5): N log-uniform
+    in [1,000, 500,000], shape square / sphere / swiss roll, 10-NN, K in {2, 4, 8, 16},
+    FP32 blocks, tolerance 1e-5.  The graphs are built before the clock starts; each request
+    is submitted at its arrival time and the library's slots admit and run the requests
+    concurrently on the device.  Latency is the library's submit-to-completion time."""
+    import numpy as np
+
+    import manifold_graphs as mg
+    from paper_2112_07862_gb300 import mge
+
+    rng = np.random.default_rng(5)
+    shapes = ["square", "sphere", "swiss_roll"]
+    reqs = []
+    for i in range(a.serve_requests):
+        n = int(round(float(np.exp(rng.uniform(np.log(1_000), np.log(500_000))))))
+        shape = shapes[int(rng.integers(3))]
+        K = int(rng.choice([2, 4, 8, 16]))
+        reqs.append((mg.manifold_graph(shape, n, 10, 500 + i), K))
+    arrivals = np.cumsum(rng.exponential(1.0 / 200.0, len(reqs)))
+
+    def request(g, K):
+        r = mge.mge_request()
+        r.n, r.row_ptr, r.col, r.w = g.n, g.row_ptr.ctypes.data, g.col.ctypes.data, g.w.ctypes.data
+        r.K, r.tol, r.precision, r.guard, r.maxiter, r.seed = K, 1e-5, mge.MGE_FP32, 0, 0, 0
+        return r
+
+    with mge.Context(0) as ctx:
+        # one small request first, so that the slots and their streams exist
+        g0 = mg.manifold_graph("square", 1_000, 10, 499)
+        t = mge.mge_submit(ctx.h, request(g0, 2))
+        mge.mge_poll(ctx.h, t, -1)
+        mge.mge_release(ctx.h, t)
+        tickets = []
+        t0 = time.perf_counter()
+        for (g, K), ta in zip(reqs, arrivals):
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(mge.mge_submit(ctx.h, request(g, K)))
+        lat, queue, ok = [], [], 0
+        for t in tickets:
+            s, r = mge.mge_poll(ctx.h, t, -1)
+            if s == mge.MGE_OK and r.status == mge.MGE_OK:
+                ok += 1
+            lat.append(r.latency_ms)
+            queue.append(r.queue_ms)
+            mge.mge_release(ctx.h, t)
+        wall = time.perf_counter() - t0
+    nodes = sum(g.n for g, _ in reqs)
+    return {"requests": len(reqs), "converged": ok, "offered_req_per_s": 200.0,
+            "served_req_per_s": len(reqs) / wall, "value": nodes / wall, "unit": UNIT,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "queue_p50_ms": float(np.percentile(queue, 50)), "queue_p99_ms": float(np.percentile(queue, 99)),
+            "nodes": int(nodes), "wall_s": wall,
+            "workload": "Poisson 200 req/s (seed 5), N log-uniform in [1000, 500000], square/sphere/swiss "
+                        "roll, 10-NN, K in {2,4,8,16}, FP32 blocks, tol 1e-5; graphs built before the clock; "
+                        "latency = submit to completion (host clock), host CSR in, host V out",
+            "slots": int(os.environ.get("MGE_SERVE_SLOTS", "4"))}
 
 
 # ---------------------------------------------------------------------------------------
@@ -367,6 +433,8 @@ def main():
     dist = Dist("nccl")
     res = run_ours(a, dist)
     if dist.rank == 0:
+        if dist.world == 1 and not a.no_serving:
+            res["serving"] = run_serving(a)
         if dist.world == 1 and not a.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(a, a.cpu_sample_n)
         print(json.dumps(res), flush=True)
