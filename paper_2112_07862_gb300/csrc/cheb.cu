@@ -259,9 +259,10 @@ cudaError_t cheb_launch(const Ctx* ctx, cudaStream_t st, const ChebArgs<T>& a, i
   int cap = 0, nst = 0;
   cheb_config<T>(max_tile_slots, &cap, &nst);
   const size_t smem = 256 + (size_t)nst * ChebLayout<T>(cap).bytes;
-  // resident CTAs per SM for this stage size (cached: the size is fixed per operator)
-  static size_t last_smem = 0;
-  static int per_sm = 1;
+  // resident CTAs per SM for this stage size (cached per host thread: the serving slots
+  // launch from several threads; the size is fixed per operator)
+  thread_local size_t last_smem = 0;
+  thread_local int per_sm = 1;
   if (smem != last_smem) {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb<T, M>, kChebThreads, smem) != cudaSuccess || b < 1)
