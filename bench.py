@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--serve-requests", type=int, default=32)
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--batch-graphs", type=int, default=64)
+    p.add_argument("--no-batch", action="store_true")
     return p.parse_args()
 
 
@@ -315,6 +317,66 @@ def run_ours(a, dist):
 
 
 # ---------------------------------------------------------------------------------------
+# the batching form: many graphs of uneven size in one graph launch (mge_embed_batch)
+# ---------------------------------------------------------------------------------------
+def run_batch(a):
+    """Graphs with N log-uniform in [2,000, 50,000], shape square / torus / swiss roll, k in
+    {8, 10, 12}, K in {4, 8} (seed 4 + index), FP32 blocks, tol 1e-5.  The operators are
+    built one after the other (each build has its own eps solve); then every embedding runs
+    as a branch of ONE CUDA graph launch, and, for comparison, one mge_embed after another.
+    Embedding throughput = sum of N / device time of the launch(es)."""
+    import numpy as np
+    import torch
+
+    import manifold_graphs as mg
+    from paper_2112_07862_gb300 import mge
+
+    rng = np.random.default_rng(4)
+    shapes = ["square", "torus", "swiss_roll"]
+    graphs = []
+    for i in range(a.batch_graphs):
+        n = int(round(float(np.exp(rng.uniform(np.log(2_000), np.log(50_000))))))
+        shape = shapes[int(rng.integers(3))]
+        k = int(rng.choice([8, 10, 12]))
+        K = int(rng.choice([4, 8]))
+        graphs.append((mg.manifold_graph(shape, n, k, 4 + i), K))
+    nodes = sum(g.n for g, _ in graphs)
+    Ks = [K for _, K in graphs]
+    with mge.Context(0) as ctx:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ops = [mge.mge_build_graph_ops(ctx.h, g.n, g.row_ptr, g.col, g.w, False, mge.ops_opts("fp32"))[0]
+               for g, _ in graphs]
+        t_build = time.perf_counter() - t0
+        eo = mge.embed_opts("fp32")
+        mge.mge_embed_batch(ctx.h, ops, Ks, a.tol, eo)            # warm-up (allocations, instantiation)
+        t0 = time.perf_counter()
+        lams, Vs, infos, s = mge.mge_embed_batch(ctx.h, ops, Ks, a.tol, eo)
+        t_batch = time.perf_counter() - t0
+        dev_batch = infos[0].solve_ms
+        t0 = time.perf_counter()
+        dev_seq = 0.0
+        for o, K in zip(ops, Ks):
+            dev_seq += mge.mge_embed(ctx.h, o, K, a.tol, eo)[2].solve_ms
+        t_seq = time.perf_counter() - t0
+        for o in ops:
+            mge.mge_ops_destroy(o)
+    iters = [i.iters for i in infos]
+    return {"graphs": len(graphs), "nodes": int(nodes), "status": int(s),
+            "converged": int(sum(1 for i in infos if i.status == 0)),
+            "value": nodes / (dev_batch / 1e3), "unit": UNIT,
+            "batch_launch_ms": dev_batch, "batch_call_ms": 1e3 * t_batch,
+            "one_by_one_device_ms": dev_seq, "one_by_one_call_ms": 1e3 * t_seq,
+            "one_by_one_value": nodes / (dev_seq / 1e3),
+            "build_ms_total": 1e3 * t_build,
+            "with_build_value": nodes / (t_build + t_batch),
+            "iters_min_max": [min(iters), max(iters)],
+            "workload": f"{len(graphs)} graphs, N log-uniform in [2000, 50000] (seed 4 + index), square/torus/"
+                        "swiss roll, k in {8,10,12}, K in {4,8}, FP32 blocks, tol 1e-5; value = sum N / device "
+                        "time of the one batch launch (embedding only); builds sequential, host CSR in"}
+
+
+# ---------------------------------------------------------------------------------------
 # the serving form: Poisson arrivals through mge_submit / mge_poll
 # ---------------------------------------------------------------------------------------
 def run_serving(a):
@@ -433,10 +495,13 @@ def main():
     dist = Dist("nccl")
     res = run_ours(a, dist)
     if dist.rank == 0:
-        if dist.world == 1 and not a.no_serving:
-            res["serving"] = run_serving(a)
+        # the oracle first, while nothing else of this process keeps the host busy
         if dist.world == 1 and not a.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(a, a.cpu_sample_n)
+        if dist.world == 1 and not a.no_batch:
+            res["batch"] = run_batch(a)
+        if dist.world == 1 and not a.no_serving:
+            res["serving"] = run_serving(a)
         print(json.dumps(res), flush=True)
     dist.close()
 

@@ -239,6 +239,27 @@ mge_status mge_embed(mge_ctx* ctx, const mge_ops* ops, int K, double tol,
                      const mge_embed_opts* opts, double* lambda, void* V,
                      mge_embed_info* info);
 
+/* Batched form of mge_embed: the first K[i] generalized eigenpairs of (A, B) of each of
+ * `count` operator handles (Sec. 4.3, Eq. 10-11, as mge_embed), computed in ONE launch of one
+ * CUDA graph in which every solve is an independent branch (its initial block and first
+ * iteration, then a device-side while loop over its iterations), so graphs of uneven size
+ * and iteration count share the GPU and each branch stops at its own convergence.
+ * ops[count], K[count]: the handles (all built on this context's device) and their K.
+ * opts: as mge_embed, shared by all solves (precision, guard, maxiter, seed, stream,
+ *   v_on_device, precond_degree); x0 must be unset; use_graph and check_every are ignored.
+ * lambda[count]: host arrays of K[i] doubles each (written, ascending).
+ * V: NULL, or count pointers (each NULL or a column-major [n_i x K[i]] FP64 buffer, host or
+ *   device per opts->v_on_device).  info: NULL or count entries; solve_ms is the device time
+ *   of the whole batch launch.  Every solve's result is the one mge_embed gives alone with
+ *   the same options (up to the order of floating-point atomics).
+ * Returns MGE_OK when every solve converged; otherwise the first failing solve's status
+ * (MGE_ENOTCONVERGED: partial results written; per-solve status in info[i].status).
+ * Errors: MGE_EINVAL (count < 1, a NULL handle or lambda, x0 set, K or width out of range),
+ * MGE_ENOMEM, MGE_EDEVICE. */
+mge_status mge_embed_batch(mge_ctx* ctx, int count, const mge_ops* const* ops, const int* K,
+                           double tol, const mge_embed_opts* opts, double* const* lambda,
+                           void* const* V, mge_embed_info* info);
+
 /* ---- serving: continuous batching of embedding requests ---------------------------- */
 
 typedef struct {

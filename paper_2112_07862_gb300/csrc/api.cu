@@ -513,6 +513,70 @@ mge_status mge_embed(mge_ctx* c, const mge_ops* o, int K, double tol, const mge_
   return s;
 }
 
+mge_status mge_embed_batch(mge_ctx* c, int count, const mge_ops* const* ops, const int* K, double tol,
+                           const mge_embed_opts* opts, double* const* lambda, void* const* V,
+                           mge_embed_info* info) {
+  if (!c || count < 1 || !ops || !K || !lambda) return MGE_EINVAL;
+  if (c->impl.closed) return MGE_EINVAL;
+  Ctx* ctx = &c->impl;
+  cudaSetDevice(ctx->device);
+  mge_embed_opts e{};
+  e.precision = MGE_FP32;
+  if (opts) e = *opts;
+  if (e.maxiter <= 0) e.maxiter = 20000;
+  if (!(tol > 0)) { set_error(ctx, "tol must be > 0"); return MGE_EINVAL; }
+  if (e.x0 && e.x0_cols > 0) { set_error(ctx, "embed_batch: x0 is not supported"); return MGE_EINVAL; }
+  const int prec = e.precision;
+  if (prec == MGE_BF16) { set_error(ctx, "BF16 blocks are not available in this build"); return MGE_EINVAL; }
+  if (prec != MGE_FP64 && prec != MGE_FP32) { set_error(ctx, "bad precision"); return MGE_EINVAL; }
+  std::vector<LobOp> lops((size_t)count);
+  std::vector<int> ms((size_t)count);
+  for (int i = 0; i < count; ++i) {
+    if (!ops[i] || !lambda[i]) { set_error(ctx, "embed_batch: NULL handle or lambda at %d", i); return MGE_EINVAL; }
+    if (K[i] < 1) { set_error(ctx, "embed_batch: K[%d] = %d", i, K[i]); return MGE_EINVAL; }
+    const int m = round_block_width(K[i] + std::max(e.guard, 0));
+    if (m < 0 || m > 24) { set_error(ctx, "embed_batch: K + guard = %d exceeds the widest block (24)", K[i] + e.guard); return MGE_EINVAL; }
+    const Ops& op = ops[i]->impl;
+    if (op.n < 2 * m) { set_error(ctx, "embed_batch: graph %d has %lld nodes; need at least %d", i, (long long)op.n, 2 * m); return MGE_EINVAL; }
+    ms[i] = m;
+    lops[i] = make_op(op, 0, prec);
+    lops[i].precond_degree = e.precond_degree > 0 ? std::min(e.precond_degree, 64) : kDefaultPrecondDegree;
+  }
+  cudaStream_t st = pick_stream(ctx, e.stream);
+  // V buffers: the caller's device arrays, or scratch copied to the caller's host arrays
+  std::vector<DevBuf<double>> vd((size_t)count);
+  std::vector<double*> vout((size_t)count, nullptr);
+  for (int i = 0; i < count && V; ++i) {
+    if (!V[i]) continue;
+    if (e.v_on_device) vout[i] = static_cast<double*>(V[i]);
+    else { MGE_TRY(vd[i].scratch(ctx, (size_t)lops[i].n * K[i], st)); vout[i] = vd[i].p; }
+  }
+  std::vector<LobResult> res((size_t)count);
+  std::vector<mge_status> sts((size_t)count, MGE_OK);
+  double ms_batch = 0;
+  MGE_TRY(lobpcg_solve_batch(ctx, st, count, lops.data(), prec, K, ms.data(), tol, e.maxiter, e.seed,
+                             vout.data(), res.data(), sts.data(), &ms_batch));
+  mge_status first = MGE_OK;
+  for (int i = 0; i < count; ++i) {
+    const mge_status s = sts[i];
+    if (s == MGE_OK || s == MGE_ENOTCONVERGED)
+      for (int k = 0; k < K[i]; ++k) lambda[i][k] = res[i].lambda[k];
+    if (V && V[i] && !e.v_on_device && (s == MGE_OK || s == MGE_ENOTCONVERGED))
+      MGE_CUDA(ctx, cudaMemcpyAsync(V[i], vd[i].p, (size_t)lops[i].n * K[i] * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (info) {
+      info[i].status = s;
+      info[i].iters = res[i].iters;
+      info[i].m = ms[i];
+      info[i].drops = res[i].drops;
+      for (int k = 0; k < 64; ++k) info[i].resid[k] = (k < K[i] && k < (int)res[i].eta.size()) ? res[i].eta[k] : 0.0;
+      info[i].solve_ms = ms_batch;
+    }
+    if (first == MGE_OK && s != MGE_OK) first = s;
+  }
+  MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  return first;
+}
+
 mge_status mge_submit(mge_ctx* c, const mge_request* req, uint64_t* ticket) {
   if (!c || !req || !ticket) return MGE_EINVAL;
   return serve_submit(&c->impl, req, ticket);

@@ -20,6 +20,8 @@
 // consumer adds the (at most MAXCL) cluster partials in FP64.  No contended atomics.
 #include "lobpcg_common.cuh"
 
+#include <memory>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -1299,6 +1301,83 @@ struct Solver {
     return MGE_OK;
   }
 
+  // Appends this solve to `graph`: the prologue (initial block and first iteration) as a
+  // child graph, then a conditional while node whose body is one iteration ending in a
+  // one-thread kernel that sets the loop condition from the device status word.  The new
+  // nodes depend on nothing else in `graph`.  per_pass receives the body's kernel launches.
+  mge_status add_loop(cudaGraph_t graph, uint64_t seed, const double* x0, int x0_cols, uint64_t* per_pass) {
+    cudaGraph_t pro = nullptr;
+    MGE_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    mge_status cap = prologue(seed, x0, x0_cols, false);
+    cudaError_t ce = cudaStreamEndCapture(st, &pro);
+    if (cap != MGE_OK) { if (pro) cudaGraphDestroy(pro); return cap; }
+    if (ce != cudaSuccess) { set_error(ctx, "graph capture failed: %s", cudaGetErrorString(ce)); return MGE_EDEVICE; }
+    cudaGraphNode_t npro = nullptr, nloop = nullptr;
+    cudaError_t e1c = cudaGraphAddChildGraphNode(&npro, graph, nullptr, 0, pro);
+    cudaGraphDestroy(pro);                      // the node holds its own copy
+    MGE_CUDA(ctx, e1c);
+    cudaGraphConditionalHandle h;
+    MGE_CUDA(ctx, cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    MGE_CUDA(ctx, cudaGraphAddNode(&nloop, graph, &npro, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    MGE_CUDA(ctx, cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const uint64_t before = ctx->kernel_launches;
+    cap = iteration(3, false);
+    if (cap == MGE_OK) {
+      k_loop_cond<<<1, 32, 0, st>>>(h, state, maxiter);
+      MGE_LAUNCHED(ctx, 1);
+    }
+    cudaGraph_t body_out = nullptr;
+    ce = cudaStreamEndCapture(st, &body_out);
+    *per_pass = ctx->kernel_launches - before;
+    ctx->kernel_launches = before;
+    if (cap != MGE_OK) return cap;
+    if (ce != cudaSuccess) {
+      set_error(ctx, "graph capture failed: %s", cudaGetErrorString(ce));
+      return MGE_EDEVICE;
+    }
+    return MGE_OK;
+  }
+
+  // After the solve has run: the status from the host copy of the device status word, the
+  // eigenvalues and backward errors, and (V_out not NULL) the sign-fixed vectors written in
+  // the caller's node order, launched on the solver's stream.
+  mge_status finish_result(const State* hst, mge_status* status, double* V_out, LobResult* res) {
+    if (hst->done == DONE_ERROR) {
+      *status = (mge_status)hst->err;
+      set_error(ctx, "LOBPCG stopped at iteration %d: %s (stage %d, kept %d)", hst->iter,
+                mge_strerror(*status), hst->bad_stage, hst->kept);
+    } else if (hst->done == DONE_MAXITER || hst->done == DONE_RUNNING) {
+      *status = MGE_ENOTCONVERGED;
+    }
+    if (getenv("MGE_PHASES")) {
+      fprintf(stderr, "[mge] n=%lld M=%d iters=%d rr_clk:", (long long)n, M, hst->iter);
+      for (int i = 0; i < 12; ++i) fprintf(stderr, " %lld", hst->rr_clk[i]);
+      fprintf(stderr, " | wprep_clk:");
+      for (int i = 0; i < 4; ++i) fprintf(stderr, " %lld", hst->wp_clk[i]);
+      fprintf(stderr, "\n");
+    }
+    res->iters = hst->iter;
+    res->drops = hst->drops;
+    res->lambda.assign(hst->lambda, hst->lambda + K);
+    res->eta.assign(hst->eta, hst->eta + K);
+    if (V_out && (*status == MGE_OK || *status == MGE_ENOTCONVERGED)) {
+      MGE_CUDA(ctx, cudaMemsetAsync(sm->vmax, 0, sizeof(sm->vmax), st));
+      MGE_CUDA(ctx, cudaMemsetAsync(sm->vidx, 0xff, sizeof(sm->vidx), st));
+      k_vmax<T><<<gridn(n * K, 256), 256, 0, st>>>(n, M, K, X.p, sm->vmax);
+      k_vidx<T><<<gridn(n * K, 256), 256, 0, st>>>(n, M, K, X.p, sm->vmax, op.row_order, sm->vidx);
+      k_write_v<T><<<gridn(n * K, 256), 256, 0, st>>>(n, M, K, X.p, sm->vidx, op.row_order, op.row_rank, V_out);
+      MGE_LAUNCHED(ctx, 3);
+      MGE_CUDA(ctx, cudaGetLastError());
+    }
+    return MGE_OK;
+  }
+
   mge_status run(int check_every, bool use_graph, uint64_t seed, const double* x0, int x0_cols,
                  double* V_out, LobResult* res) {
     cudaEvent_t e0, e1;
@@ -1320,43 +1399,9 @@ struct Solver {
     cudaGraph_t graph = nullptr;
     uint64_t per_pass = 0;
     if (loop_graph) {
-      cudaGraph_t pro = nullptr;
-      MGE_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      mge_status cap = prologue(seed, x0, x0_cols, false);
-      cudaError_t ce = cudaStreamEndCapture(st, &pro);
-      if (cap != MGE_OK) { if (pro) cudaGraphDestroy(pro); return cap; }
-      if (ce != cudaSuccess) { set_error(ctx, "graph capture failed: %s", cudaGetErrorString(ce)); return MGE_EDEVICE; }
       MGE_CUDA(ctx, cudaGraphCreate(&graph, 0));
-      cudaGraphNode_t npro = nullptr, nloop = nullptr;
-      cudaError_t e1c = cudaGraphAddChildGraphNode(&npro, graph, nullptr, 0, pro);
-      cudaGraphDestroy(pro);                      // the node holds its own copy
-      MGE_CUDA(ctx, e1c);
-      cudaGraphConditionalHandle h;
-      MGE_CUDA(ctx, cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
-      cudaGraphNodeParams cp = {};
-      cp.type = cudaGraphNodeTypeConditional;
-      cp.conditional.handle = h;
-      cp.conditional.type = cudaGraphCondTypeWhile;
-      cp.conditional.size = 1;
-      MGE_CUDA(ctx, cudaGraphAddNode(&nloop, graph, &npro, nullptr, 1, &cp));
-      cudaGraph_t body = cp.conditional.phGraph_out[0];
-      MGE_CUDA(ctx, cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-      const uint64_t before = ctx->kernel_launches;
-      cap = iteration(3, false);
-      if (cap == MGE_OK) {
-        k_loop_cond<<<1, 32, 0, st>>>(h, state, maxiter);
-        MGE_LAUNCHED(ctx, 1);
-      }
-      cudaGraph_t body_out = nullptr;
-      ce = cudaStreamEndCapture(st, &body_out);
-      per_pass = ctx->kernel_launches - before;
-      ctx->kernel_launches = before;
-      if (cap != MGE_OK) { cudaGraphDestroy(graph); return cap; }
-      if (ce != cudaSuccess) {
-        cudaGraphDestroy(graph);
-        set_error(ctx, "graph capture failed: %s", cudaGetErrorString(ce));
-        return MGE_EDEVICE;
-      }
+      const mge_status ag = add_loop(graph, seed, x0, x0_cols, &per_pass);
+      if (ag != MGE_OK) { cudaGraphDestroy(graph); return ag; }
       MGE_CUDA(ctx, cudaGraphInstantiate(&gexec, graph, 0));
       MGE_CUDA(ctx, cudaGraphLaunch(gexec, st));
     } else {
@@ -1430,33 +1475,7 @@ struct Solver {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
     MGE_CUDA(ctx, cudaEventRecord(e1, st));
-    if (hst->done == DONE_ERROR) {
-      status = (mge_status)hst->err;
-      set_error(ctx, "LOBPCG stopped at iteration %d: %s (stage %d, kept %d)", hst->iter,
-                mge_strerror(status), hst->bad_stage, hst->kept);
-    } else if (hst->done == DONE_MAXITER || hst->done == DONE_RUNNING) {
-      status = MGE_ENOTCONVERGED;
-    }
-    if (getenv("MGE_PHASES")) {
-      fprintf(stderr, "[mge] n=%lld M=%d iters=%d rr_clk:", (long long)n, M, hst->iter);
-      for (int i = 0; i < 12; ++i) fprintf(stderr, " %lld", hst->rr_clk[i]);
-      fprintf(stderr, " | wprep_clk:");
-      for (int i = 0; i < 4; ++i) fprintf(stderr, " %lld", hst->wp_clk[i]);
-      fprintf(stderr, "\n");
-    }
-    res->iters = hst->iter;
-    res->drops = hst->drops;
-    res->lambda.assign(hst->lambda, hst->lambda + K);
-    res->eta.assign(hst->eta, hst->eta + K);
-    if (V_out && (status == MGE_OK || status == MGE_ENOTCONVERGED)) {
-      MGE_CUDA(ctx, cudaMemsetAsync(sm->vmax, 0, sizeof(sm->vmax), st));
-      MGE_CUDA(ctx, cudaMemsetAsync(sm->vidx, 0xff, sizeof(sm->vidx), st));
-      k_vmax<T><<<gridn(n * K, 256), 256, 0, st>>>(n, M, K, X.p, sm->vmax);
-      k_vidx<T><<<gridn(n * K, 256), 256, 0, st>>>(n, M, K, X.p, sm->vmax, op.row_order, sm->vidx);
-      k_write_v<T><<<gridn(n * K, 256), 256, 0, st>>>(n, M, K, X.p, sm->vidx, op.row_order, op.row_rank, V_out);
-      MGE_LAUNCHED(ctx, 3);
-      MGE_CUDA(ctx, cudaGetLastError());
-    }
+    MGE_TRY(finish_result(hst, &status, V_out, res));
     MGE_CUDA(ctx, cudaStreamSynchronize(st));
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
@@ -1472,13 +1491,12 @@ struct Solver {
   }
 };
 
+// Buffers, the operators' entry counts and the kernels' shared-memory limits of one solve
 template <typename T, int M>
-mge_status solve_m(Ctx* ctx, cudaStream_t st, const LobOp& op, int K, double tol, int maxiter, uint64_t seed,
-                   int check_every, bool use_graph, const double* x0, int x0_cols, double* V_out,
-                   LobResult* res) {
-  Solver<T, M> s(ctx, st, op, K);
-  s.tol = tol;
-  s.maxiter = maxiter;
+mge_status prepare_solver(Solver<T, M>& s) {
+  Ctx* ctx = s.ctx;
+  cudaStream_t st = s.st;
+  const LobOp& op = s.op;
   MGE_TRY(s.setup());
   int64_t nnz = 0;
   MGE_CUDA(ctx, cudaMemcpyAsync(&nnz, op.ptr + op.n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -1493,7 +1511,55 @@ mge_status solve_m(Ctx* ctx, cudaStream_t st, const LobOp& op, int K, double tol
   MGE_CUDA(ctx, (spmm_configure<T, M>()));
   MGE_CUDA(ctx, (cheb_configure<T, M>()));
   MGE_CUDA(ctx, rr_configure());
+  return MGE_OK;
+}
+
+template <typename T, int M>
+mge_status solve_m(Ctx* ctx, cudaStream_t st, const LobOp& op, int K, double tol, int maxiter, uint64_t seed,
+                   int check_every, bool use_graph, const double* x0, int x0_cols, double* V_out,
+                   LobResult* res) {
+  Solver<T, M> s(ctx, st, op, K);
+  s.tol = tol;
+  s.maxiter = maxiter;
+  MGE_TRY(prepare_solver(s));
   return s.run(check_every, use_graph, seed, x0, x0_cols, V_out, res);
+}
+
+// One solve of a batch (solves of several widths and precisions share one graph)
+struct BatchItem {
+  virtual ~BatchItem() {}
+  virtual mge_status prepare() = 0;
+  virtual mge_status add(cudaGraph_t g, uint64_t seed) = 0;
+  virtual const State* device_state() const = 0;
+  virtual mge_status finish(const State* hst, mge_status* status, double* V_out, LobResult* res) = 0;
+  uint64_t per_pass = 0;
+};
+
+template <typename T, int M>
+struct BatchItemT : BatchItem {
+  Solver<T, M> s;
+  BatchItemT(Ctx* c, cudaStream_t st, const LobOp& op, int K, double tol, int maxiter) : s(c, st, op, K) {
+    s.tol = tol;
+    s.maxiter = maxiter;
+  }
+  mge_status prepare() override { return prepare_solver(s); }
+  mge_status add(cudaGraph_t g, uint64_t seed) override { return s.add_loop(g, seed, nullptr, 0, &per_pass); }
+  const State* device_state() const override { return s.state; }
+  mge_status finish(const State* hst, mge_status* status, double* V_out, LobResult* res) override {
+    return s.finish_result(hst, status, V_out, res);
+  }
+};
+
+template <typename T>
+BatchItem* make_batch_item_t(Ctx* ctx, cudaStream_t st, const LobOp& op, int K, int m, double tol, int maxiter) {
+  switch (m) {
+    case 4: return new BatchItemT<T, 4>(ctx, st, op, K, tol, maxiter);
+    case 8: return new BatchItemT<T, 8>(ctx, st, op, K, tol, maxiter);
+    case 12: return new BatchItemT<T, 12>(ctx, st, op, K, tol, maxiter);
+    case 16: return new BatchItemT<T, 16>(ctx, st, op, K, tol, maxiter);
+    case 24: return new BatchItemT<T, 24>(ctx, st, op, K, tol, maxiter);
+    default: return nullptr;
+  }
 }
 
 template <typename T>
@@ -1545,6 +1611,82 @@ mge_status lobpcg_solve(Ctx* ctx, cudaStream_t st, const LobOp& op, int precisio
     return solve_t<float>(ctx, st, op, K, m, tol, maxiter, seed, check_every, use_graph, x0_dev, x0_cols, V_out, res);
   set_error(ctx, "precision %d not supported by the solver", precision);
   return MGE_EINVAL;
+}
+
+// Several solves in one CUDA graph: each solve is a branch of its own (prologue, then its
+// conditional while loop) with no edge to the others, so one launch runs them side by side
+// and each branch stops when its own solve has converged.
+mge_status lobpcg_solve_batch(Ctx* ctx, cudaStream_t st, int count, const LobOp* ops, int precision, const int* K,
+                              const int* m, double tol, int maxiter, uint64_t seed, double* const* V_out,
+                              LobResult* res, mge_status* status, double* batch_ms) {
+  using namespace lob;
+  if (precision != MGE_FP64 && precision != MGE_FP32) {
+    set_error(ctx, "precision %d not supported by the solver", precision);
+    return MGE_EINVAL;
+  }
+  std::vector<std::unique_ptr<BatchItem>> items;
+  items.reserve(count);
+  for (int i = 0; i < count; ++i) {
+    if (m[i] > MAXM || m[i] < 4) { set_error(ctx, "batch item %d: block width %d out of range", i, m[i]); return MGE_EINVAL; }
+    if (K[i] < 1 || K[i] > m[i]) { set_error(ctx, "batch item %d: K = %d out of range", i, K[i]); return MGE_EINVAL; }
+    if (ops[i].n < 2 * m[i]) {
+      set_error(ctx, "batch item %d: n = %lld too small for block width %d", i, (long long)ops[i].n, m[i]);
+      return MGE_EINVAL;
+    }
+    BatchItem* it = precision == MGE_FP64 ? make_batch_item_t<double>(ctx, st, ops[i], K[i], m[i], tol, maxiter)
+                                          : make_batch_item_t<float>(ctx, st, ops[i], K[i], m[i], tol, maxiter);
+    if (!it) { set_error(ctx, "batch item %d: unsupported block width %d", i, m[i]); return MGE_EINVAL; }
+    items.emplace_back(it);
+  }
+  for (auto& it : items) MGE_TRY(it->prepare());
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  MGE_CUDA(ctx, cudaGraphCreate(&graph, 0));
+  for (auto& it : items) {
+    const mge_status a = it->add(graph, seed);
+    if (a != MGE_OK) { cudaGraphDestroy(graph); return a; }
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) { set_error(ctx, "batch graph instantiation: %s", cudaGetErrorString(ie)); return MGE_EDEVICE; }
+  State* hst = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  mge_status out = MGE_OK;
+  auto fail = [&](cudaError_t e, const char* what) {
+    set_error(ctx, "%s: %s", what, cudaGetErrorString(e));
+    out = MGE_EDEVICE;
+  };
+  cudaError_t e;
+  if ((e = cudaMallocHost(&hst, sizeof(State) * (size_t)count)) != cudaSuccess) fail(e, "cudaMallocHost");
+  if (out == MGE_OK && (e = cudaEventCreate(&e0)) != cudaSuccess) fail(e, "cudaEventCreate");
+  if (out == MGE_OK && (e = cudaEventCreate(&e1)) != cudaSuccess) fail(e, "cudaEventCreate");
+  if (out == MGE_OK && (e = cudaEventRecord(e0, st)) != cudaSuccess) fail(e, "cudaEventRecord");
+  if (out == MGE_OK && (e = cudaGraphLaunch(gexec, st)) != cudaSuccess) fail(e, "cudaGraphLaunch");
+  if (out == MGE_OK && (e = cudaEventRecord(e1, st)) != cudaSuccess) fail(e, "cudaEventRecord");
+  for (int i = 0; i < count && out == MGE_OK; ++i)
+    if ((e = cudaMemcpyAsync(&hst[i], items[i]->device_state(), sizeof(State), cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
+      fail(e, "cudaMemcpyAsync");
+  if (out == MGE_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) fail(e, "batch solve");
+  if (out == MGE_OK) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    *batch_ms = ms;
+    for (int i = 0; i < count; ++i) {
+      ctx->kernel_launches += items[i]->per_pass * (uint64_t)hst[i].loops;
+      status[i] = MGE_OK;
+      const mge_status f = items[i]->finish(&hst[i], &status[i], V_out ? V_out[i] : nullptr, &res[i]);
+      if (f != MGE_OK) status[i] = f;
+      res[i].status = status[i];
+      res[i].ms = ms;
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) fail(e, "batch results");
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (hst) cudaFreeHost(hst);
+  cudaGraphExecDestroy(gexec);
+  return out;
 }
 
 // Y = A X with X already in the library's node order; row r of the product goes to row

@@ -269,6 +269,12 @@ mge_status lobpcg_solve(Ctx* ctx, cudaStream_t st, const LobOp& op, int precisio
                         double tol, int maxiter, uint64_t seed, int check_every, bool use_graph,
                         const double* x0_dev /*col-major n x x0_cols*/, int x0_cols,
                         double* V_out, LobResult* res);
+// Runs `count` solves (operator ops[i], K[i] pairs, block width m[i]) as branches of one CUDA
+// graph launched once on st; status[i] and res[i] per solve, batch_ms the launch's device time.
+// V_out (NULL, or an array of device pointers that may hold NULLs) as in lobpcg_solve.
+mge_status lobpcg_solve_batch(Ctx* ctx, cudaStream_t st, int count, const LobOp* ops, int precision, const int* K,
+                              const int* m, double tol, int maxiter, uint64_t seed, double* const* V_out,
+                              LobResult* res, mge_status* status, double* batch_ms);
 
 mge_status spmm_apply(Ctx* ctx, cudaStream_t st, const LobOp& op, int precision, int m,
                       const void* X, void* Y);

@@ -25,7 +25,7 @@ PRECISION = {"fp64": MGE_FP64, "fp32": MGE_FP32, "bf16": MGE_BF16}
 EXPORTS = [
     "mge_create", "mge_destroy", "mge_strerror", "mge_ctx_last_error", "mge_ctx_stats",
     "mge_ctx_set_timing", "mge_ctx_reset_stats", "mge_build_graph_ops", "mge_ops_destroy",
-    "mge_ops_info", "mge_ops_export", "mge_ops_node_order", "mge_ops_apply", "mge_ops_apply_inplace", "mge_embed", "mge_submit", "mge_poll",
+    "mge_ops_info", "mge_ops_export", "mge_ops_node_order", "mge_ops_apply", "mge_ops_apply_inplace", "mge_embed", "mge_embed_batch", "mge_submit", "mge_poll",
     "mge_release",
 ]
 
@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH):
         "mge_ops_apply": (i, [vp, vp, i, i, i, vp, vp, vp]),
         "mge_ops_apply_inplace": (i, [vp, vp, i, i, i, vp, vp]),
         "mge_embed": (i, [vp, vp, i, d, C.POINTER(mge_embed_opts), vp, vp, C.POINTER(mge_embed_info)]),
+        "mge_embed_batch": (i, [vp, i, vp, vp, d, C.POINTER(mge_embed_opts), vp, vp, vp]),
         "mge_submit": (i, [vp, C.POINTER(mge_request), C.POINTER(u64)]),
         "mge_poll": (i, [vp, u64, i, C.POINTER(mge_result)]),
         "mge_release": (i, [vp, u64]),
@@ -246,6 +247,30 @@ def mge_embed(ctx, ops, K: int, tol: float, opts: mge_embed_opts | None = None, 
     return lam, V, ei, s
 
 
+def mge_embed_batch(ctx, ops, K, tol: float, opts: mge_embed_opts | None = None, V=None):
+    """Batched mge_embed over the handles `ops` with K[i] pairs each, in one graph launch.
+    Returns (list of lambda arrays, list of V, list of mge_embed_info, status).  V: None
+    (host arrays [K_i, n_i] are allocated unless opts.v_on_device), or a list of host numpy
+    float64 arrays / device tensors [K_i, n_i] (column-major n_i x K_i), entries may be None."""
+    count = len(ops)
+    K = [int(k) for k in K]
+    if len(K) != count:
+        raise ValueError("ops and K differ in length")
+    on_dev = opts is not None and opts.v_on_device
+    lams = [np.empty(k, np.float64) for k in K]
+    if V is None:
+        V = [None] * count if on_dev else [np.empty((k, mge_ops_info(o).n), np.float64) for o, k in zip(ops, K)]
+    handles = (C.c_void_p * count)(*[o.value if isinstance(o, C.c_void_p) else o for o in ops])
+    ks = (C.c_int * count)(*K)
+    lam_p = (C.c_void_p * count)(*[_ptr(a) for a in lams])
+    v_p = (C.c_void_p * count)(*[_ptr(v) for v in V])
+    infos = (mge_embed_info * count)()
+    s = load().mge_embed_batch(ctx, count, handles, ks, float(tol), C.byref(opts) if opts is not None else None,
+                               lam_p, v_p, infos)
+    _check(ctx, s, "mge_embed_batch", ok=(MGE_OK, MGE_ENOTCONVERGED))
+    return lams, V, list(infos), s
+
+
 def mge_submit(ctx, req: mge_request) -> int:
     t = C.c_uint64()
     s = load().mge_submit(ctx, C.byref(req), C.byref(t))
@@ -327,6 +352,10 @@ class Context:
     def embed(self, ops, K, tol, **kw):
         lam, V, info, s = mge_embed(self.h, ops.h, K, tol, embed_opts(**kw))
         return lam, V.T if isinstance(V, np.ndarray) else V, info, s
+
+    def embed_batch(self, ops, K, tol, **kw):
+        lams, Vs, infos, s = mge_embed_batch(self.h, [o.h for o in ops], K, tol, embed_opts(**kw))
+        return lams, [v.T if isinstance(v, np.ndarray) else v for v in Vs], infos, s
 
     def stats(self):
         return mge_ctx_stats(self.h)
