@@ -134,6 +134,23 @@ typedef struct {
 mge_status mge_build_graph_ops(mge_ctx* ctx, int64_t n, const int64_t* row_ptr,
                                const int32_t* col, const double* w, int on_device,
                                const mge_ops_opts* opts, mge_ops** out);
+
+/* Builds the operators of many graphs (each exactly as mge_build_graph_ops, Sec. 4) with
+ * `workers` host threads (0 = 8), each issuing its builds on a CUDA stream of its own, so
+ * that the builds' kernels, their eps solves and their host round trips overlap.
+ * n, row_ptr, col, w: count entries each (host or device pointers per on_device; device
+ *   inputs written on opts->stream are waited for first).  opts: shared; its stream is not
+ *   used by the builds.
+ * out[count]: handles (NULL where a build failed); status[count] (may be NULL): each build's
+ *   own status (MGE_EDEGENERATE with a valid handle as in mge_build_graph_ops).
+ * Returns MGE_OK when every build produced a handle, else the first failing status.
+ * Every build's result equals the one mge_build_graph_ops gives alone (up to the order of
+ * floating-point atomics in its eps solve). */
+mge_status mge_build_graph_ops_batch(mge_ctx* ctx, int count, const int64_t* n,
+                                     const int64_t* const* row_ptr, const int32_t* const* col,
+                                     const double* const* w, int on_device,
+                                     const mge_ops_opts* opts, int workers, mge_ops** out,
+                                     mge_status* status);
 mge_status mge_ops_destroy(mge_ops* ops);
 
 typedef struct {

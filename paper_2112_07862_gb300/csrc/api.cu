@@ -2,6 +2,7 @@
 #include "mge_internal.cuh"
 
 #include <algorithm>
+#include <thread>
 #include <vector>
 
 #include <cstdarg>
@@ -220,6 +221,50 @@ mge_status mge_build_graph_ops(mge_ctx* c, int64_t n, const int64_t* row_ptr, co
   }
   *out = o;
   return s;
+}
+
+mge_status mge_build_graph_ops_batch(mge_ctx* c, int count, const int64_t* n, const int64_t* const* row_ptr,
+                                     const int32_t* const* col, const double* const* w, int on_device,
+                                     const mge_ops_opts* opts, int workers, mge_ops** out, mge_status* status) {
+  if (!c || count < 1 || !n || !row_ptr || !col || !w || !out) return MGE_EINVAL;
+  Ctx* ctx = &c->impl;
+  if (ctx->closed) return MGE_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return MGE_EDEVICE;
+  for (int i = 0; i < count; ++i) out[i] = nullptr;
+  // device inputs may still be in flight on the caller's stream
+  if (on_device) MGE_CUDA(ctx, cudaStreamSynchronize(pick_stream(ctx, opts ? opts->stream : nullptr)));
+  std::vector<mge_status> sts((size_t)count, MGE_EDEVICE);    // stays so for a graph no worker took
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return; }
+    mge_ops_opts oo{};
+    oo.precision = MGE_FP32;
+    if (opts) oo = *opts;
+    oo.stream = s;
+    for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1))
+      sts[i] = mge_build_graph_ops(c, n[i], row_ptr[i], col[i], w[i], on_device, &oo, &out[i]);
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  };
+  const int nw = std::max(1, std::min(workers > 0 ? workers : 8, count));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nw; ++t) {
+    try {
+      pool.emplace_back(work);
+    } catch (...) {
+      break;
+    }
+  }
+  work();
+  for (auto& t : pool) t.join();
+  mge_status first = MGE_OK;
+  for (int i = 0; i < count; ++i) {
+    if (status) status[i] = sts[i];
+    if (first == MGE_OK && sts[i] != MGE_OK && sts[i] != MGE_EDEGENERATE) first = sts[i];
+  }
+  return first;
 }
 
 mge_status mge_ops_destroy(mge_ops* o) {

@@ -24,7 +24,7 @@ PRECISION = {"fp64": MGE_FP64, "fp32": MGE_FP32, "bf16": MGE_BF16}
 # every symbol include/mge.h declares
 EXPORTS = [
     "mge_create", "mge_destroy", "mge_strerror", "mge_ctx_last_error", "mge_ctx_stats",
-    "mge_ctx_set_timing", "mge_ctx_reset_stats", "mge_build_graph_ops", "mge_ops_destroy",
+    "mge_ctx_set_timing", "mge_ctx_reset_stats", "mge_build_graph_ops", "mge_build_graph_ops_batch", "mge_ops_destroy",
     "mge_ops_info", "mge_ops_export", "mge_ops_node_order", "mge_ops_apply", "mge_ops_apply_inplace", "mge_embed", "mge_embed_batch", "mge_submit", "mge_poll",
     "mge_release",
 ]
@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH):
         "mge_ctx_set_timing": (i, [vp, i]),
         "mge_ctx_reset_stats": (i, [vp]),
         "mge_build_graph_ops": (i, [vp, i64, vp, vp, vp, i, C.POINTER(mge_ops_opts), C.POINTER(vp)]),
+        "mge_build_graph_ops_batch": (i, [vp, i, vp, vp, vp, vp, i, C.POINTER(mge_ops_opts), i, vp, vp]),
         "mge_ops_destroy": (i, [vp]),
         "mge_ops_info": (i, [vp, C.POINTER(mge_ops_info_t)]),
         "mge_ops_export": (i, [vp, vp, vp, vp, vp, vp, vp, vp, vp, i]),
@@ -183,6 +184,30 @@ def mge_build_graph_ops(ctx, n, row_ptr, col, w, on_device: bool = False, opts: 
                                    C.byref(opts) if opts is not None else None, C.byref(h))
     _check(ctx, s, "mge_build_graph_ops", ok=(MGE_OK, MGE_EDEGENERATE))
     return h, s
+
+
+def mge_build_graph_ops_batch(ctx, graphs, on_device: bool = False, opts: mge_ops_opts | None = None,
+                              workers: int = 0):
+    """graphs: a list of (n, row_ptr, col, w) (numpy arrays, or torch CUDA tensors when
+    on_device).  Returns (list of handles, None where a build failed; list of statuses;
+    status)."""
+    count = len(graphs)
+    keep = []
+    ns = (C.c_int64 * count)()
+    rps, cols, ws = (C.c_void_p * count)(), (C.c_void_p * count)(), (C.c_void_p * count)()
+    for i, (n, rp, col, w) in enumerate(graphs):
+        if not on_device:
+            rp = np.ascontiguousarray(rp, dtype=np.int64)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            w = np.ascontiguousarray(w, dtype=np.float64)
+        keep.append((rp, col, w))
+        ns[i], rps[i], cols[i], ws[i] = int(n), _ptr(rp), _ptr(col), _ptr(w)
+    out = (C.c_void_p * count)()
+    sts = (C.c_int * count)()
+    s = load().mge_build_graph_ops_batch(ctx, count, ns, rps, cols, ws, 1 if on_device else 0,
+                                         C.byref(opts) if opts is not None else None, int(workers), out, sts)
+    _check(ctx, s, "mge_build_graph_ops_batch", ok=(MGE_OK, MGE_EDEGENERATE))
+    return [C.c_void_p(h) if h else None for h in out], list(sts), s
 
 
 def mge_ops_destroy(ops) -> int:
@@ -352,6 +377,11 @@ class Context:
     def embed(self, ops, K, tol, **kw):
         lam, V, info, s = mge_embed(self.h, ops.h, K, tol, embed_opts(**kw))
         return lam, V.T if isinstance(V, np.ndarray) else V, info, s
+
+    def build_batch(self, graphs, workers=0, **kw):
+        hs, sts, s = mge_build_graph_ops_batch(self.h, [(g.n, g.row_ptr, g.col, g.w) for g in graphs], False,
+                                               ops_opts(**kw), workers)
+        return [Ops(h, st) for h, st in zip(hs, sts)]
 
     def embed_batch(self, ops, K, tol, **kw):
         lams, Vs, infos, s = mge_embed_batch(self.h, [o.h for o in ops], K, tol, embed_opts(**kw))

@@ -71,3 +71,25 @@ def test_batch_rejects_bad_arguments(ctx, gpu_lib):
     assert e.value.status == mge.MGE_EINVAL
     assert mge.load().mge_embed_batch(ctx.h, 0, None, None, 1e-6, None, None, None, None) == mge.MGE_EINVAL
     ops.close()
+
+
+def test_batch_build_equals_single_builds(ctx):
+    """mge_build_graph_ops_batch (builds on several host threads and streams at once) gives
+    each graph the operators mge_build_graph_ops gives it alone: the integer structure and
+    T bit for bit, eps and the values up to the order of the eps solve's atomics."""
+    graphs = [mg.manifold_graph(s, n, k, 40 + i) for i, (s, n, k, _) in enumerate(GRAPHS)]
+    graphs.append(mg.ring(10))                       # even ring: two-hop graph disconnected
+    single = [ctx.build(g, precision="fp32") for g in graphs]
+    batch = ctx.build_batch(graphs, workers=3, precision="fp32")
+    for g, a, b in zip(graphs, single, batch):
+        assert b.h is not None and b.status == a.status
+        ea, eb = a.export(), b.export()
+        for key in ("a_ptr", "a_col", "T"):
+            assert np.array_equal(ea[key], eb[key]), key
+        ia, ib = a.info(), b.info()
+        assert ib.eps == pytest.approx(ia.eps, rel=1e-9, abs=1e-300)
+        assert ib.mu == pytest.approx(ia.mu, rel=1e-9, abs=1e-300)
+        assert np.allclose(eb["a_val"], ea["a_val"], rtol=1e-9, atol=1e-15)
+        assert np.allclose(eb["b"], ea["b"], rtol=1e-9, atol=0)
+    for o in single + batch:
+        o.close()
