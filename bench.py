@@ -427,17 +427,19 @@ def run_serving(a):
             if dt > 0:
                 time.sleep(dt)
             tickets.append(mge.mge_submit(ctx.h, request(g, K)))
-        lat, queue, ok = [], [], 0
+        lat, queue, ok, statuses = [], [], 0, {}
         for t in tickets:
             s, r = mge.mge_poll(ctx.h, t, -1)
             if s == mge.MGE_OK and r.status == mge.MGE_OK:
                 ok += 1
+            key = mge.mge_strerror(r.status if s == mge.MGE_OK else s)
+            statuses[key] = statuses.get(key, 0) + 1
             lat.append(r.latency_ms)
             queue.append(r.queue_ms)
             mge.mge_release(ctx.h, t)
         wall = time.perf_counter() - t0
     nodes = sum(g.n for g, _ in reqs)
-    return {"requests": len(reqs), "converged": ok, "offered_req_per_s": 200.0,
+    return {"requests": len(reqs), "converged": ok, "statuses": statuses, "offered_req_per_s": 200.0,
             "served_req_per_s": len(reqs) / wall, "value": nodes / wall, "unit": UNIT,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "queue_p50_ms": float(np.percentile(queue, 50)), "queue_p99_ms": float(np.percentile(queue, 99)),

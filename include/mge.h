@@ -151,6 +151,9 @@ mge_status mge_build_graph_ops_batch(mge_ctx* ctx, int count, const int64_t* n,
                                      const double* const* w, int on_device,
                                      const mge_ops_opts* opts, int workers, mge_ops** out,
                                      mge_status* status);
+/* Releases the handle's device arrays.  Call it once no call that uses the handle is in
+ * progress on any thread; every call has finished its device work on the handle when it
+ * returns.  Performs no device-wide synchronisation. */
 mge_status mge_ops_destroy(mge_ops* ops);
 
 typedef struct {

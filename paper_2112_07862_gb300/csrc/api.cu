@@ -271,10 +271,12 @@ mge_status mge_ops_destroy(mge_ops* o) {
   if (!o) return MGE_EINVAL;
   Ctx* ctx = o->impl.ctx;
   if (ctx) cudaSetDevice(ctx->device);
-  // the arrays may be in use on any stream: wait for the device, then return the pooled ones
-  // on the default stream (the stream of the build may be gone)
-  cudaDeviceSynchronize();
-  o->impl.each_buffer([](auto& b) { if (b.pooled) b.st = nullptr; });
+  // Every call that uses the handle has finished its device work when it returns (each one
+  // synchronises its stream), so the pooled arrays go back to the pool at once, ordered on
+  // this thread's per-thread default stream (the stream of the build may be gone).  No
+  // device-wide synchronisation: that would invalidate a graph capture another host thread
+  // (a serving slot) has in progress.
+  o->impl.each_buffer([](auto& b) { if (b.pooled) b.st = cudaStreamPerThread; });
   delete o;
   if (ctx) ctx_release(ctx);
   return MGE_OK;

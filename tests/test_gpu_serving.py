@@ -77,3 +77,31 @@ def test_budget_serialises_but_completes(gpu_lib):
             s, r = mge.mge_poll(ctx.h, t, -1)
             assert s == 0 and r.status == 0
             mge.mge_release(ctx.h, t)
+
+
+def test_eight_slots_every_request_matches_alone(gpu_lib, monkeypatch):
+    """Eight slots: the builds, graph captures and handle releases of different requests
+    interleave on eight host threads, and every request still converges to its result
+    alone (a device-wide synchronisation in one slot would break another slot's capture)."""
+    mge = gpu_lib
+    specs = [("square", 1500, 4), ("sphere", 2500, 8), ("swiss_roll", 3000, 8), ("torus", 2000, 2),
+             ("square", 4000, 16), ("sphere", 1200, 4), ("swiss_roll", 5000, 4), ("torus", 3500, 8)] * 2
+    graphs = [(mg.manifold_graph(shape, n, 10, 60 + i), K) for i, (shape, n, K) in enumerate(specs)]
+    with mge.Context(0) as ctx:
+        alone = []
+        for g, K in graphs:
+            ops = ctx.build(g, precision="fp32")
+            lam, V, info, s = ctx.embed(ops, K, 1e-6, precision="fp32", guard=4)
+            alone.append((lam, V))
+            ops.close()
+    monkeypatch.setenv("MGE_SERVE_SLOTS", "8")
+    with mge.Context(0) as ctx:
+        tickets = [mge.mge_submit(ctx.h, request(mge, g, K)) for g, K in graphs]
+        for (g, K), t, (lam0, V0) in zip(graphs, tickets, alone):
+            s, r = mge.mge_poll(ctx.h, t, -1)
+            assert s == 0 and r.status == 0, (s, r.status, mge.mge_ctx_last_error(ctx.h))
+            lam = np.ctypeslib.as_array(r.lambda_, shape=(K,)).copy()
+            V = np.ctypeslib.as_array(r.V, shape=(K, g.n)).T.copy()
+            assert np.allclose(lam, lam0, rtol=1e-10, atol=0)
+            assert np.max(np.abs(V - V0)) < 1e-8
+            assert mge.mge_release(ctx.h, t) == 0
