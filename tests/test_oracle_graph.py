@@ -188,6 +188,26 @@ def test_operator_invariants(g):
     assert ev[1] == pytest.approx(ops.eps, rel=1e-10)
 
 
+@pytest.mark.parametrize("g", MANIFOLD[:4], ids=lambda g: g.name)
+def test_a_quadratic_form_by_brute_force(g):
+    """Eq. 6 with the per-node split of Eq. 12: x^T A x = sum over edges w_ij (x_i - x_j)^2
+    - mu sum_i (1/T_i) sum_{j in T_i} (x_i - x_j)^2 + eps |x|^2, the sums taken in plain
+    Python over the adjacency lists and brute-force two-hop sets (the Laplacian reading of
+    Eq. 5), against the oracle's assembled A."""
+    ops = go.from_graph(g)
+    ref = brute_two_hop(g)
+    x = np.random.default_rng(5).standard_normal(g.n)
+    glr = 0.0
+    for i in range(g.n):
+        for p in range(g.row_ptr[i], g.row_ptr[i + 1]):
+            j = int(g.col[p])
+            if i < j:
+                glr += g.w[p] * (x[i] - x[j]) ** 2
+    two_hop = sum(sum((x[i] - x[j]) ** 2 for j in ref[i]) / len(ref[i]) for i in range(g.n) if ref[i])
+    direct = glr - ops.mu * two_hop + ops.eps * float(x @ x)
+    assert x @ (ops.A @ x) == pytest.approx(direct, rel=1e-11)
+
+
 @pytest.mark.parametrize("g", MANIFOLD, ids=lambda g: g.name)
 def test_mu_is_largest_value_keeping_discs_nonnegative(g):
     """Eq. 7 directly: every disc left end of L - mu Q + eps I is >= 0 at mu, and some
@@ -251,3 +271,20 @@ def test_planted_transposed_two_hop_rule_breaks_brute_force():
     bad.sort_indices()
     ref = brute_two_hop(g)
     assert any(bad.indices[bad.indptr[i]:bad.indptr[i + 1]].tolist() != ref[i] for i in range(g.n))
+
+
+def test_planted_sign_of_mu_q_breaks_quadratic_form_pin():
+    """A = L + mu Q + eps I (wrong sign of the two-hop term) keeps A 1 = eps 1 and symmetry,
+    but the brute-force quadratic form of Eq. 6 / Eq. 12 catches it."""
+    g = mg.manifold_graph("square", 300, 8, 1)
+    ops = go.from_graph(g)
+    ref = brute_two_hop(g)
+    A_bad = (ops.L + ops.mu * ops.Q + ops.eps * sp.identity(g.n)).tocsr()
+    assert np.max(np.abs(A_bad @ np.ones(g.n) - ops.eps)) < 1e-12
+    x = np.random.default_rng(5).standard_normal(g.n)
+    rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    once = rows < g.col
+    glr = float(np.sum(g.w[once] * (x[rows[once]] - x[g.col[once]]) ** 2))
+    two_hop = sum(sum((x[i] - x[j]) ** 2 for j in ref[i]) / len(ref[i]) for i in range(g.n) if ref[i])
+    direct = glr - ops.mu * two_hop + ops.eps * float(x @ x)
+    assert x @ (A_bad @ x) != pytest.approx(direct, rel=1e-6)
