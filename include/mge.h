@@ -187,9 +187,12 @@ mge_status mge_ops_export(const mge_ops* ops, int64_t* a_ptr, int32_t* a_col, do
 mge_status mge_ops_node_order(const mge_ops* ops, int32_t* order, int on_device);
 
 /* Y = A X (which = 0) or Y = Q X (which = 1) with the library's SpMM kernel in the given
- * precision; X and Y are row-major [n x m] blocks of that precision (double, float, or
- * bfloat16 bits as uint16), device pointers, m in {4, 8, 12, 16, 24, 32}.  Test and
- * measurement entry point for the SpMM of the iteration. */
+ * precision (MGE_FP64 or MGE_FP32); X and Y are row-major [n x m] blocks of that precision
+ * (double or float), m in {4, 8, 12, 16, 24}, device pointers of the context's device,
+ * 16-byte aligned, rows in the caller's node order.  Test and measurement entry point for
+ * the SpMM of the iteration (Sec. 4.3: the products A q of the LOBPCG solve).
+ * Errors: MGE_EINVAL (bad which, precision or width; a pointer that is misaligned, host
+ * memory or on another device -- checked on the host before anything runs), MGE_EDEVICE. */
 mge_status mge_ops_apply(mge_ctx* ctx, const mge_ops* ops, int which, int precision, int m,
                          const void* X, void* Y, void* stream);
 
@@ -200,8 +203,10 @@ mge_status mge_ops_apply(mge_ctx* ctx, const mge_ops* ops, int which, int precis
  * the work on its other streams.  The paper has no counterpart; it is a service entry
  * point around the SpMM of the iteration (same kernel, same results as mge_ops_apply).
  *
- * XY: device pointer, row-major [n x m] block of the given precision (MGE_FP64 or
- * MGE_FP32), 16-byte aligned, m in {4, 8, 12, 16, 24}; overwritten with the product.
+ * XY: device pointer of the context's device, row-major [n x m] block of the given
+ * precision (MGE_FP64 or MGE_FP32), 16-byte aligned, m in {4, 8, 12, 16, 24}; overwritten
+ * with the product.  A misaligned, host or foreign pointer is rejected with MGE_EINVAL
+ * before anything runs.
  * The copy of the block the product needs goes into one fixed 32 MiB device array inside
  * the library (not counted in the context's HBM budget); a block whose size
  * n * m * sizeof(element) exceeds 32 MiB is rejected with MGE_EINVAL.  Nothing in the array
@@ -218,7 +223,7 @@ mge_status mge_ops_apply_inplace(mge_ctx* ctx, const mge_ops* ops, int which, in
 typedef struct {
   int         precision;      /* mge_precision of the blocks (default MGE_FP32)             */
   int         guard;          /* extra columns beyond K; m = K + guard is rounded up to a
-                                 supported block width (4, 8, 12, 16, 24, 32)              */
+                                 supported block width (4, 8, 12, 16, 24)                  */
   int         maxiter;        /* default 20000                                             */
   uint64_t    seed;           /* seed of the initial block when x0 is NULL                  */
   int         check_every;    /* iterations between host checks of convergence (default 16)*/
@@ -253,7 +258,7 @@ typedef struct {
  * opts->v_on_device) with the first K generalized eigenpairs of (A, B) of `ops`.
  * Convergence: every returned column has backward error
  *   eta = ||A x - lambda B x||_2 / ((||A||_G + |lambda| max b) ||x||_2) <= tol.
- * Errors: MGE_EINVAL (K < 1, K + guard > 32, n < m), MGE_ENOTCONVERGED (partial results
+ * Errors: MGE_EINVAL (K < 1, K + guard > 24, n < m), MGE_ENOTCONVERGED (partial results
  * written), MGE_ECHOLESKY, MGE_ENOTFINITE, MGE_ENOMEM, MGE_EDEVICE.  `info` may be NULL. */
 mge_status mge_embed(mge_ctx* ctx, const mge_ops* ops, int K, double tol,
                      const mge_embed_opts* opts, double* lambda, void* V,

@@ -146,6 +146,29 @@ def fiedler_value(Q: sp.csr_matrix, n_components: int, tol: float = 1e-12, seed:
     return float(res.lam[0])
 
 
+def fiedler_value_sparse(Q: sp.csr_matrix, n_components: int) -> tuple[float, float]:
+    """eps = lambda_2(Q) for large N without an iteration tolerance of the oracle's own.
+
+    The two smallest eigenvalues of the Laplacian Q by ARPACK's shift-invert Lanczos
+    (scipy ``eigsh`` on Q - sigma I with sigma just below 0, a library step at machine
+    precision).  Returns (eps, residual) where residual = ||Q v - eps v|| / ||Q||_G for the
+    returned unit vector v, so a caller can check the value actually converged.
+    """
+    import scipy.sparse.linalg as spla
+    n = Q.shape[0]
+    if n < 2 or n_components > 1:
+        return 0.0, 0.0
+    Q = sp.csr_matrix(Q)
+    absrow = np.asarray(abs(Q).sum(axis=1)).ravel()
+    qn = float(np.max(absrow))
+    lam, U = spla.eigsh(Q.tocsc(), k=2, sigma=-1e-9 * qn, which="LM", tol=0.0,
+                        v0=np.linspace(1.0, 2.0, n))
+    j = int(np.argsort(lam)[1])
+    v = U[:, j] / np.linalg.norm(U[:, j])
+    res = float(np.linalg.norm(Q @ v - lam[j] * v)) / qn
+    return float(lam[j]), res
+
+
 def mu_value(Q: sp.csr_matrix, eps: float) -> float:
     """Eq. 9: mu_i = eps / (Q_ii - sum_{j != i} Q_ij), mu = min over rows with a positive denominator."""
     if eps == 0.0:

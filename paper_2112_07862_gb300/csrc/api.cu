@@ -85,6 +85,32 @@ static cudaStream_t pick_stream(Ctx* ctx, void* s) {
   return s ? static_cast<cudaStream_t>(s) : ctx->stream;
 }
 
+// Widths the operator-product entry points support (the SpMM kernel's instantiations).
+static bool apply_width_ok(int m) { return m == 4 || m == 8 || m == 12 || m == 16 || m == 24; }
+
+// A block pointer handed to mge_ops_apply[_inplace]: 16-byte aligned (the kernels read
+// rows with 16-byte loads and bulk copies) and device memory of the context's device (a
+// host or foreign pointer would fault inside the kernel).  Checked on the host before any
+// launch, so a bad pointer returns MGE_EINVAL with the buffer untouched.
+static mge_status check_block_ptr(Ctx* ctx, const void* p, const char* who, const char* name) {
+  if (reinterpret_cast<uintptr_t>(p) & 15u) {
+    set_error(ctx, "%s: %s is not 16-byte aligned", who, name);
+    return MGE_EINVAL;
+  }
+  cudaPointerAttributes a{};
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(ctx, "%s: %s is not a CUDA pointer", who, name);
+    return MGE_EINVAL;
+  }
+  if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != ctx->device) {
+    set_error(ctx, "%s: %s is not device memory of device %d", who, name, ctx->device);
+    return MGE_EINVAL;
+  }
+  return MGE_OK;
+}
+
 }  // namespace mge
 
 using namespace mge;
@@ -466,7 +492,9 @@ mge_status mge_ops_apply(mge_ctx* c, const mge_ops* o, int which, int precision,
     set_error(ctx, "apply: precision %d not supported", precision);
     return MGE_EINVAL;
   }
-  if (round_block_width(m) != m) { set_error(ctx, "apply: unsupported width %d", m); return MGE_EINVAL; }
+  if (!apply_width_ok(m)) { set_error(ctx, "apply: unsupported width %d (4, 8, 12, 16 or 24)", m); return MGE_EINVAL; }
+  MGE_TRY(check_block_ptr(ctx, X, "apply", "X"));
+  MGE_TRY(check_block_ptr(ctx, Y, "apply", "Y"));
   cudaStream_t st = pick_stream(ctx, stream);
   LobOp l = make_op(o->impl, which, precision);
   MGE_TRY(spmm_apply(ctx, st, l, precision, m, X, Y));
@@ -484,7 +512,11 @@ mge_status mge_ops_apply_inplace(mge_ctx* c, const mge_ops* o, int which, int pr
     set_error(ctx, "apply_inplace: precision %d not supported", precision);
     return MGE_EINVAL;
   }
-  if (round_block_width(m) != m) { set_error(ctx, "apply_inplace: unsupported width %d", m); return MGE_EINVAL; }
+  if (!apply_width_ok(m)) {
+    set_error(ctx, "apply_inplace: unsupported width %d (4, 8, 12, 16 or 24)", m);
+    return MGE_EINVAL;
+  }
+  MGE_TRY(check_block_ptr(ctx, XY, "apply_inplace", "XY"));
   cudaStream_t st = pick_stream(ctx, stream);
   LobOp l = make_op(o->impl, which, precision);
   MGE_TRY(spmm_apply_inplace(ctx, st, l, precision, m, XY));

@@ -244,8 +244,25 @@ def mge_ops_node_order(ops):
     return order
 
 
+def _check_block(ops, precision: int, m: int, t, name: str):
+    """A block handed to an apply entry point: a contiguous CUDA tensor of shape (n, m)
+    whose dtype is the precision's element type (the C entry point itself checks the
+    pointer's alignment and memory type, but cannot see the tensor's size or dtype)."""
+    import torch
+    want = {MGE_FP64: torch.float64, MGE_FP32: torch.float32}.get(precision)
+    n = mge_ops_info(ops).n
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise MgeError(MGE_EINVAL, f"{name} must be a contiguous CUDA tensor")
+    if want is not None and t.dtype != want:
+        raise MgeError(MGE_EINVAL, f"{name} has dtype {t.dtype}; precision {precision} needs {want}")
+    if tuple(t.shape) != (n, m):
+        raise MgeError(MGE_EINVAL, f"{name} has shape {tuple(t.shape)}; expected {(n, m)}")
+
+
 def mge_ops_apply(ctx, ops, which: int, precision: int, m: int, X, Y, stream=None) -> int:
     """Y = A X (which=0) or Q X (which=1); X, Y torch CUDA tensors [n, m] row-major."""
+    _check_block(ops, precision, m, X, "X")
+    _check_block(ops, precision, m, Y, "Y")
     s = load().mge_ops_apply(ctx, ops, which, precision, m, _ptr(X), _ptr(Y), stream)
     return _check(ctx, s, "mge_ops_apply")
 
@@ -253,6 +270,7 @@ def mge_ops_apply(ctx, ops, which: int, precision: int, m: int, X, Y, stream=Non
 def mge_ops_apply_inplace(ctx, ops, which: int, precision: int, m: int, XY, stream=None) -> int:
     """XY <- A XY (which=0) or Q XY (which=1) in place; XY a torch CUDA tensor [n, m].  The
     library allocates nothing for it (a fixed 32 MiB device array holds the copy)."""
+    _check_block(ops, precision, m, XY, "XY")
     s = load().mge_ops_apply_inplace(ctx, ops, which, precision, m, _ptr(XY), stream)
     return _check(ctx, s, "mge_ops_apply_inplace")
 

@@ -79,6 +79,7 @@ def test_products_are_in_the_callers_order(gpu_lib, ctx, prec):
     k = ctx.build(g, keep_order=True, **kw)
     dt = torch.float64 if prec == "fp64" else torch.float32
     X = torch.randn(g.n, 8, generator=torch.Generator().manual_seed(3), dtype=torch.float64).to("cuda", dt)
+    torch.cuda.synchronize()      # the library works on its own stream: X must be complete
     tol = dict(rtol=1e-12, atol=1e-12) if prec == "fp64" else dict(rtol=2e-5, atol=2e-5)
     for which in (0, 1):
         Ya, Yk = torch.empty_like(X), torch.empty_like(X)
@@ -88,6 +89,7 @@ def test_products_are_in_the_callers_order(gpu_lib, ctx, prec):
         torch.testing.assert_close(Ya, Yk, **tol)
         # and the same through the in-place entry point
         XY = X.clone()
+        torch.cuda.synchronize()
         mge.mge_ops_apply_inplace(ctx.h, a.h, which, mge.PRECISION[prec], 8, XY)
         torch.cuda.synchronize()
         torch.testing.assert_close(XY, Ya, rtol=0.0, atol=0.0)

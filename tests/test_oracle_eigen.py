@@ -126,3 +126,62 @@ def test_planted_wrong_b_scaling_breaks_generalized_residual(square1k):
     V_bad = U[:, :3] * s[:, None]
     eta = ge.backward_errors(ops.A, ops.b, lam[:3], V_bad)
     assert np.max(eta) > 1e-6
+
+
+def test_gershgorin_norm_exact_on_hand_computed_matrices():
+    """||A||_G = max_i (A_ii + sum_{j != i} |A_ij|), worked by hand:
+    rows of [[4,-1,0],[-1,5,-2],[0,-2,3]] give 4+1, 5+3, 3+2 -> 8 (the middle row);
+    [[2,0.5,-0.25],[0.5,1,0],[-0.25,0,6]] gives 2.75, 1.5, 6.25 -> 6.25 (the last row,
+    so a norm taken from the first row, or doubled, or without the diagonal, fails)."""
+    A = np.array([[4.0, -1.0, 0.0], [-1.0, 5.0, -2.0], [0.0, -2.0, 3.0]])
+    assert ge.gershgorin_norm(A) == 8.0
+    A2 = np.array([[2.0, 0.5, -0.25], [0.5, 1.0, 0.0], [-0.25, 0.0, 6.0]])
+    assert ge.gershgorin_norm(A2) == 6.25
+
+
+def test_sparse_geneig_matches_dense_definition():
+    """Shift-invert Lanczos against the dense eigendecomposition of B^-1/2 A B^-1/2."""
+    ops = go.from_graph(mg.manifold_graph("swiss_roll", 1500, 10, 9))
+    d = ge.dense_geneig(ops.A, ops.b, 6)
+    s = ge.sparse_geneig(ops.A, ops.b, 6)
+    np.testing.assert_allclose(s.lam, d.lam, rtol=1e-10)
+    for j in range(6):
+        assert ge.subspace_angle(s.V[:, [j]], d.V[:, [j]]) < 1e-7
+    VBV = s.V.T @ (ops.b[:, None] * s.V)
+    assert np.max(np.abs(VBV - np.eye(6))) < 1e-10
+    assert np.max(ge.backward_errors(ops.A, ops.b, s.lam, s.V)) < 1e-13
+
+
+def test_sparse_geneig_odd_ring_closed_form():
+    """Odd ring C_N (b = 1): lambda_k = (2 - 2cos t) - mu (2 - 2cos 2t) + eps, t = 2 pi k / N,
+    eps = 2 - 2cos(2 pi / N) and mu = eps / 4 (the closed form of Sec. 4 on the ring)."""
+    N = 4001
+    ops = go.build_graph_ops(*_ring_csr(N), eps_override=2 - 2 * np.cos(2 * np.pi / N))
+    eps = ops.eps
+    mu = eps / 4
+    t = 2 * np.pi * np.arange(N) / N
+    lam_all = np.sort((2 - 2 * np.cos(t)) - mu * (2 - 2 * np.cos(2 * t)) + eps)
+    s = ge.sparse_geneig(ops.A, ops.b, 5)
+    np.testing.assert_allclose(s.lam, lam_all[:5], rtol=1e-9)
+    assert ops.mu == pytest.approx(mu, rel=1e-12)
+
+
+def test_fiedler_value_sparse_odd_ring_and_dense():
+    N = 4001
+    g = mg.ring(N)
+    t_ptr, t_col, T = go.two_hop_sets(g.n, g.row_ptr, g.col)
+    Q = go.q_matrix(g.n, t_ptr, t_col)
+    eps, res = go.fiedler_value_sparse(Q, 1)
+    assert eps == pytest.approx(2 - 2 * np.cos(2 * np.pi / N), rel=1e-9)
+    assert res < 1e-12
+    g2 = mg.manifold_graph("square", 1200, 8, 4)
+    t_ptr, t_col, T = go.two_hop_sets(g2.n, g2.row_ptr, g2.col)
+    Q2 = go.q_matrix(g2.n, t_ptr, t_col)
+    eps2, _ = go.fiedler_value_sparse(Q2, 1)
+    assert eps2 == pytest.approx(np.linalg.eigvalsh(Q2.toarray())[1], rel=1e-10)
+    assert go.fiedler_value_sparse(Q2, 2) == (0.0, 0.0)
+
+
+def _ring_csr(N):
+    g = mg.ring(N)
+    return g.n, g.row_ptr, g.col, g.w

@@ -5,6 +5,9 @@ held in a fixed device array, so on the same input its output must equal
 mge_ops_apply's bit for bit (tolerance zero).  Checked on two calls in a row, since every
 call shares the array; blocks larger than the array are rejected before anything is
 touched.  The file name sorts last so that the test also runs after all other GPU tests.
+
+The library runs on its own (non-blocking) stream, so every block built by torch on its
+current stream is synchronised before it is handed over.
 """
 import numpy as np
 import pytest
@@ -32,8 +35,9 @@ def test_inplace_apply_equals_apply_on_two_calls(gpu_lib, prec, m, which):
     for call in range(2):
         X = _block(g.n, m, dt, gen)
         Y = torch.empty_like(X)
-        mge.mge_ops_apply(ctx.h, ops.h, which, mge.PRECISION[prec], m, X, Y)
         XY = X.clone()
+        torch.cuda.synchronize()
+        mge.mge_ops_apply(ctx.h, ops.h, which, mge.PRECISION[prec], m, X, Y)
         mge.mge_ops_apply_inplace(ctx.h, ops.h, which, mge.PRECISION[prec], m, XY)
         torch.cuda.synchronize()
         torch.testing.assert_close(XY, Y, rtol=0.0, atol=0.0, msg=f"call {call}")
@@ -48,6 +52,7 @@ def test_inplace_apply_limit(gpu_lib):
     ops = ctx.build(mg.path(n), precision="fp64")  # two-hop graph disconnected: eps = 0
     assert ops.status == mge.MGE_EDEGENERATE
     big = torch.ones(n, 24, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
     assert big.numel() * 8 > SCRATCH_BYTES
     with pytest.raises(mge.MgeError) as e:
         mge.mge_ops_apply_inplace(ctx.h, ops.h, 0, mge.MGE_FP64, 24, big)
@@ -59,6 +64,7 @@ def test_inplace_apply_limit(gpu_lib):
     for _ in range(2):
         X = _block(n, 24, torch.float32, gen)
         Y = torch.empty_like(X)
+        torch.cuda.synchronize()
         mge.mge_ops_apply(ctx.h, ops.h, 0, mge.MGE_FP32, 24, X, Y)
         mge.mge_ops_apply_inplace(ctx.h, ops.h, 0, mge.MGE_FP32, 24, X)
         torch.cuda.synchronize()
