@@ -62,7 +62,7 @@ typedef enum {
 /* Arithmetic of the iterated blocks X, W, P and of the stored matrix values.
  *   MGE_FP64  everything in FP64, including the Rayleigh-Ritz eigensolve (cyclic Jacobi).
  *   MGE_FP32  FP32 blocks and SpMM; Gram sums in FP32 with compensation, reduced across
- *             the GPU in FP64; residual norms and backward errors in FP64; the
+ *             the GPU in FP64; residual norms in FP64; the
  *             Rayleigh-Ritz scaling in FP64 and its eigensolve in FP32 on the inverse
  *             pencil (the wanted smallest eigenvalues become the largest, which FP32
  *             resolves to relative accuracy).
@@ -103,8 +103,8 @@ typedef struct {
   double   eps_override;
   int      mu_override_set;   /* nonzero: use mu_override instead of Eq. 9                  */
   double   mu_override;
-  double   eps_tol;           /* backward-error tolerance of the eps solve (0 = default:
-                                 1e-12 in FP64, 2e-7 in FP32/BF16)                          */
+  double   eps_tol;           /* relative-residual tolerance of the eps solve (the measure
+                                 of mge_embed; 0 = default: 1e-10 in FP64, 1e-5 otherwise)  */
   int      eps_guard;         /* extra LOBPCG columns for the eps solve (default 7)         */
   int      eps_maxiter;       /* default 20000                                              */
   uint64_t seed;              /* seed of the eps solve's initial block                      */
@@ -167,7 +167,7 @@ typedef struct {
   int     degenerate;         /* eps forced to 0                                            */
   int     two_hop_components; /* connected components of (V, T)                             */
   int     eps_iters;          /* LOBPCG iterations of the eps solve                         */
-  double  eps_resid;          /* its final backward error                                   */
+  double  eps_resid;          /* its final relative residual (see mge_embed)               */
   double  build_ms;           /* device time of the whole build                             */
 } mge_ops_info_t;
 
@@ -250,14 +250,22 @@ typedef struct {
   int    iters;               /* LOBPCG iterations                                         */
   int    m;                   /* block width used                                          */
   int    drops;               /* iterations whose Rayleigh-Ritz basis dropped a direction   */
-  double resid[64];           /* backward error eta_k of each returned pair (k < K)         */
+  double resid[64];           /* relative residual rho_k of each returned pair (k < K)      */
   double solve_ms;            /* device time of the solve                                  */
 } mge_embed_info;
 
 /* Fills lambda[K] (host, ascending) and V (column-major [n x K] FP64, host or device per
  * opts->v_on_device) with the first K generalized eigenpairs of (A, B) of `ops`.
- * Convergence: every returned column has backward error
- *   eta = ||A x - lambda B x||_2 / ((||A||_G + |lambda| max b) ||x||_2) <= tol.
+ * Convergence: every returned column has relative residual
+ *   rho = ||A x - lambda B x||_{B^-1} / ((|lambda| + u ||A||_G) ||x||_B) <= tol,
+ * the residual of the symmetric form B^-1/2 A B^-1/2 relative to the eigenvalue (ARPACK's
+ * criterion), with ||v||_{B^-1}^2 = sum v_i^2 / b_i, ||x||_B^2 = sum b_i x_i^2,
+ * ||A||_G = max_i (A_ii + r_i) and u the unit roundoff of the block precision (2^-53 or
+ * 2^-24) as a floor for lambda = 0.  rho <= tol bounds each eigenvalue's relative error by
+ * about tol^2 |lambda| / gap and each vector's angle by about tol |lambda| / gap (gap: the
+ * distance to the nearest other eigenvalue).  The residual is the one the iteration
+ * carries (A x from its recurrences); a residual recomputed from the returned FP32 vectors
+ * also holds their rounding noise, about u ||A|| / |lambda|.
  * Errors: MGE_EINVAL (K < 1, K + guard > 24, n < m), MGE_ENOTCONVERGED (partial results
  * written), MGE_ECHOLESKY, MGE_ENOTFINITE, MGE_ENOMEM, MGE_EDEVICE.  `info` may be NULL. */
 mge_status mge_embed(mge_ctx* ctx, const mge_ops* ops, int K, double tol,

@@ -18,7 +18,12 @@ P^T B P = I, the dimensionally consistent form of the q_i^T B q_j condition).
   is the constraint when computing lambda_2 of a Laplacian.
 
 Convergence and accuracy measures (the paper gives none; these are the readings used):
-  backward error  eta = ||A x - lambda B x||_2 / ((||A||_G + |lambda| max_i b_i) ||x||_2)
+  relative residual  rho = ||A x - lambda B x||_{B^-1} / ((|lambda| + u ||A||_G) ||x||_B),
+      the residual of B^{-1/2} A B^{-1/2} relative to the eigenvalue (ARPACK's rule for
+      symmetric problems), u the unit roundoff: the stopping rule of the GPU solver;
+  backward error  eta = ||A x - lambda B x||_2 / ((||A||_G + |lambda| max_i b_i) ||x||_2),
+      a normwise measure that a rounded vector also satisfies (used to check returned
+      FP32 vectors, whose rounding noise the relative residual would magnify);
   with ||A||_G = max_i (A_ii + r_i), a Gershgorin bound on ||A||_2.
 
 Sign convention for returned vectors: the entry of largest magnitude is positive (the
@@ -83,6 +88,21 @@ def backward_errors(A, b, lam, V, normA=None) -> np.ndarray:
     return rn / ((normA + np.abs(lam) * np.max(b)) * xn)
 
 
+def relative_residuals(A, b, lam, V, normA=None, unit_roundoff: float = 2.0 ** -53) -> np.ndarray:
+    """rho_k = ||A v - lambda B v||_{B^-1} / ((|lambda| + u ||A||_G) ||v||_B) for each column.
+
+    The residual of the symmetric form C = B^{-1/2} A B^{-1/2} (with u = B^{1/2} v, C u -
+    lambda u = B^{-1/2} r) relative to the eigenvalue -- the stopping rule ARPACK applies to
+    symmetric problems -- with the unit roundoff u times ||A||_G as a floor for lambda = 0.
+    Norms: ||r||_{B^-1}^2 = sum r_i^2 / b_i, ||v||_B^2 = sum b_i v_i^2."""
+    if normA is None:
+        normA = gershgorin_norm(A)
+    R = A @ V - (b[:, None] * V) * lam[None, :]
+    rn = np.sqrt(np.sum(R * R / b[:, None], axis=0))
+    vn = np.sqrt(np.sum(b[:, None] * V * V, axis=0))
+    return rn / ((np.abs(lam) + unit_roundoff * normA) * vn)
+
+
 def _b_orthonormalize(V, b):
     """Cholesky QR in the B inner product; returns None when the Gram is not positive definite."""
     G = V.T @ (b[:, None] * V)
@@ -102,12 +122,15 @@ def _apply_constraints(V, Y, b):
 
 def lobpcg(A, b: np.ndarray, K: int, *, guard: int = 0, Y=None, tol: float = 1e-10,
            maxiter: int = 20000, seed: int = 0, X0=None, precond: str = "jacobi",
-           normA: float | None = None) -> EigResult:
+           normA: float | None = None, measure: str = "backward") -> EigResult:
     """Textbook FP64 LOBPCG for the K smallest eigenpairs of (A, diag(b)).
 
     m = K + guard columns are iterated; convergence is judged on the first K by the
-    backward error eta <= tol.
+    backward error eta <= tol (measure="backward") or by the relative residual
+    rho <= tol (measure="relative", see ``relative_residuals``).
     """
+    if measure not in ("backward", "relative"):
+        raise ValueError(measure)
     A = sp.csr_matrix(A)
     n = A.shape[0]
     m = K + guard
@@ -131,8 +154,12 @@ def lobpcg(A, b: np.ndarray, K: int, *, guard: int = 0, Y=None, tol: float = 1e-
     for it in range(1, maxiter + 1):
         BX = b[:, None] * X
         R = AX - BX * lam[None, :]
-        rn = np.linalg.norm(R, axis=0)
-        eta = rn / ((normA + np.abs(lam) * bmax) * np.linalg.norm(X, axis=0))
+        if measure == "backward":
+            rn = np.linalg.norm(R, axis=0)
+            eta = rn / ((normA + np.abs(lam) * bmax) * np.linalg.norm(X, axis=0))
+        else:
+            rn = np.sqrt(np.sum(R * R / b[:, None], axis=0))
+            eta = rn / ((np.abs(lam) + 2.0 ** -53 * normA) * np.sqrt(np.sum(BX * X, axis=0)))
         if np.all(eta[:K] <= tol):
             return EigResult(lam[:K].copy(), fix_signs(X[:, :K]), it - 1, True, eta[:K], restarts)
         W = T[:, None] * R

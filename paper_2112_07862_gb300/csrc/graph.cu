@@ -857,7 +857,7 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
       int guard = o.eps_guard > 0 ? o.eps_guard : (n >= 2 * 8 ? 7 : 3);
       int m = round_block_width(1 + guard);
       if (m > n - 1) m = -1;
-      double tol = o.eps_tol > 0 ? o.eps_tol : (o.precision == MGE_FP64 ? 1e-12 : 2e-7);
+      double tol = o.eps_tol > 0 ? o.eps_tol : (o.precision == MGE_FP64 ? 1e-10 : 1e-5);
       int maxit = o.eps_maxiter > 0 ? o.eps_maxiter : 20000;
       if (m < 0) {
         set_error(ctx, "graph too small for the eps solve block (n = %lld)", (long long)n);

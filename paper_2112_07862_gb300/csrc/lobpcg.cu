@@ -819,12 +819,15 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads) k_update(
         st4(a.APo + row * M + c0, ap);
       }
       T r[4], w[4];
+      // norms for the convergence test: ||r||_{B^-1}^2 = sum r^2 / b and ||x||_B^2 = sum b x^2
+      // (1/b in FP32: the norms only meet a tolerance)
+      const T ib = (T)(1.0f / (float)bi);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         r[q] = ax[q] - bi * x[q] * sLam[c0 + q];
         w[q] = r[q] * di;
-        pr[q] += r[q] * r[q];
-        px[q] += x[q] * x[q];
+        pr[q] += r[q] * r[q] * ib;
+        px[q] += bi * x[q] * x[q];
       }
       st4(a.Wr + row * M + c0, w);
     }

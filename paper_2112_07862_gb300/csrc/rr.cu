@@ -1422,8 +1422,13 @@ __global__ void __launch_bounds__(kThreads) k_wprep(WprepArgs a) {
       const double rn2 = a.ncl_n == 1 ? sm->partN[0][k] : sum_strided(&sm->partN[0][k], a.ncl_n, 2 * MAXM);
       const double xn2 = a.ncl_n == 1 ? sm->partN[0][MAXM + k] : sum_strided(&sm->partN[0][MAXM + k], a.ncl_n, 2 * MAXM);
       const double lam = sm->lam[k];
-      // backward error; FP32 arithmetic is ample for a number compared with a tolerance
-      const float eta = sqrtf((float)rn2) / (((float)a.norm + fabsf((float)lam) * (float)a.bmax) * sqrtf((float)xn2));
+      // relative residual rho = ||A x - lam B x||_{B^-1} / ((|lam| + u ||A||_G) ||x||_B): the
+      // residual of the symmetric form B^-1/2 A B^-1/2 relative to the eigenvalue, with the
+      // block precision's unit roundoff u times ||A||_G as a floor for lam = 0.  FP32
+      // arithmetic is ample for a number compared with a tolerance.
+      const float ufloor = a.is_double ? 1.1102230e-16f : 5.9604645e-8f;
+      const float den = fabsf((float)lam) + ufloor * (float)a.norm;
+      const float eta = sqrtf((float)rn2) / (den * sqrtf((float)xn2));
       bad |= !isfinite(eta) || !isfinite(lam);
       a.st->eta[k] = (double)eta;
       a.st->lambda[k] = lam;

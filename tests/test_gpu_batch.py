@@ -47,7 +47,7 @@ def test_batch_member_matches_dense_oracle(ctx):
     d = oe.dense_geneig(ref.A, ref.b, 5)
     big = mg.manifold_graph("swiss_roll", 6000, 10, 8)
     ops = [ctx.build(big, precision="fp32"), ctx.build(g, precision="fp32")]
-    lams, Vs, infos, s = ctx.embed_batch(ops, [8, 4], 1e-7, precision="fp32", guard=4)
+    lams, Vs, infos, s = ctx.embed_batch(ops, [8, 4], 1e-6, precision="fp32", guard=4)
     assert s == 0
     lam, V = lams[1], Vs[1]
     assert np.max(np.abs(lam - d.lam[:4]) / d.lam[:4]) <= 1e-4

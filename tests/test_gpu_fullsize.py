@@ -67,6 +67,7 @@ def test_config_swiss_roll_200k_fp32(gpu_lib):
         lam, V, ei, s = ctx.embed(ops, K, 1e-5, precision="fp32")
         ops.close()
     assert s == 0
+    assert np.all(np.asarray(ei.resid[:K]) <= 1e-5)     # the solver's own relative residual
     t_ptr, t_col, T = og.two_hop_sets(g.n, g.row_ptr, g.col)
     assert np.array_equal(ex["T"], T)
     a_ptr, a_col = og.a_structure(g.n, g.row_ptr, g.col, t_ptr, t_col)

@@ -4,8 +4,8 @@ Tolerances: CSR structure (row pointers, ascending columns, explicit diagonal) a
 two-hop counts T_i are compared bit for bit.  FP64 values are sums of at most a row's worth
 of terms in a different order than the oracle's assembly, so they agree to a few ulp times
 the row length; the tests use 1e-13 relative.  eps comes from two different eigensolvers
-(dense in the oracle, LOBPCG on the GPU): 1e-9 relative in FP64, 2e-5 in FP32 (its backward
-error tolerance is 2e-7 on a spectrum whose scale is ||Q||).  mu, A's two-hop values and b
+(dense in the oracle, LOBPCG on the GPU): 1e-9 relative in FP64, 2e-5 in FP32 (the default
+relative-residual tolerances, 1e-10 and 1e-5, bound eps's error far below these).  mu, A's two-hop values and b
 inherit eps's relative error.
 """
 import numpy as np

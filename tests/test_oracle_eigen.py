@@ -185,3 +185,33 @@ def test_fiedler_value_sparse_odd_ring_and_dense():
 def _ring_csr(N):
     g = mg.ring(N)
     return g.n, g.row_ptr, g.col, g.w
+
+
+def test_relative_residual_zero_for_exact_pairs_and_scale_invariant(swiss2k):
+    ops = swiss2k
+    d = ge.dense_geneig(ops.A, ops.b, 5)
+    rho = ge.relative_residuals(ops.A, ops.b, d.lam, d.V)
+    assert np.max(rho) < 1e-9
+    # a perturbation of size delta along another eigenvector gives
+    # rho = delta |lam_j - lam_k| / (lam_k sqrt(1 + delta^2)) exactly (B-orthonormal pairs)
+    delta = 1e-3
+    v = d.V[:, 1] + delta * d.V[:, 3]
+    rq = float(v @ (ops.A @ v)) / float(v @ (ops.b * v))
+    rho1 = ge.relative_residuals(ops.A, ops.b, np.array([rq]), v[:, None])[0]
+    # exact value from the two-term expansion: r = (lam1 - rq) B v1 + delta (lam3 - rq) B v3
+    l1, l3 = d.lam[1], d.lam[3]
+    rn = np.sqrt((l1 - rq) ** 2 + (delta * (l3 - rq)) ** 2)
+    want = rn / ((abs(rq) + 2.0 ** -53 * ge.gershgorin_norm(ops.A)) * np.sqrt(1 + delta ** 2))
+    assert rho1 == pytest.approx(want, rel=1e-6)
+    # scaling A and lambda together leaves rho unchanged; scaling V leaves it unchanged
+    rho2 = ge.relative_residuals(3.0 * ops.A, ops.b, np.array([3.0 * rq]), 7.0 * v[:, None])[0]
+    assert rho2 == pytest.approx(rho1, rel=1e-9)
+
+
+def test_lobpcg_relative_measure_converges_to_the_dense_pairs(swiss2k):
+    ops = swiss2k
+    d = ge.dense_geneig(ops.A, ops.b, 5)
+    r = ge.lobpcg(ops.A, ops.b, 4, guard=2, tol=1e-9, seed=3, measure="relative")
+    assert r.converged
+    np.testing.assert_allclose(r.lam, d.lam[:4], rtol=1e-12)
+    assert np.max(ge.relative_residuals(ops.A, ops.b, r.lam, r.V)) <= 1e-9
