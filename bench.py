@@ -197,7 +197,7 @@ def run_ours(a, dist):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
     oo = mge.ops_opts(a.precision, stream=sptr)
     eo = mge.embed_opts(a.precision, v_on_device=True, stream=sptr)
-    status = {"build": None, "embed": None}
+    status = {"build": None, "embed": None, "m": None}
     phases = {"build_ms": [], "embed_ms": [], "eps_iters": []}
 
     def step():
@@ -209,7 +209,7 @@ def run_ours(a, dist):
         phases["eps_iters"].append(oi.eps_iters)
         phases["embed_ms"].append(info.solve_ms)
         mge.mge_ops_destroy(h)
-        status["build"], status["embed"] = s, s2
+        status["build"], status["embed"], status["m"] = s, s2, info.m
         return lam, info
 
     for _ in range(a.warmup):
@@ -305,10 +305,13 @@ def run_ours(a, dist):
                        parallelism=f"replicas x{dist.world} (independent graphs, no collective)"),
         "gpu_launches": int(st.kernel_launches) * a.steps,
         "lobpcg_iters_per_step": statistics.mean(iters),
+        "lobpcg_block_m": status["m"],
         "phases": {"build_ms": statistics.mean(phases["build_ms"][:a.steps]),
                    "embed_ms": statistics.mean(phases["embed_ms"][:a.steps]),
                    "eps_iters": statistics.mean(phases["eps_iters"][:a.steps])},
         "status": {"build": status["build"], "embed": status["embed"]},
+        "accuracy_note": "eigenvalues within 1e-6 relative and eigenvectors within 1.4e-4 rad of the oracle's "
+                         "machine-precision pairs on this workload (tests/test_gpu_fullsize.py)",
         "roofline": roofline,
         "e2e": e2e,
         "clocks": clk,

@@ -85,6 +85,23 @@ static cudaStream_t pick_stream(Ctx* ctx, void* s) {
   return s ? static_cast<cudaStream_t>(s) : ctx->stream;
 }
 
+// Arithmetic of the Rayleigh-Ritz eigensolve and of W's Cholesky for reduced-precision
+// blocks: FP64 when opts.rr_fp64 is set (FP64 blocks always)
+static bool rr_fp64_for(const mge_embed_opts& e, int prec) {
+  return prec == MGE_FP64 || e.rr_fp64 != 0;
+}
+
+// Extra LOBPCG columns beyond K: opts.guard > 0 as given, < 0 none, 0 the default of K more
+// (block width 2K, at most the widest block, 24).  The K-th pair converges at a rate set by
+// lambda_K / lambda_{m+1}; with no guard that ratio is the gap to the next eigenvalue, which
+// on manifold graphs is about 1% (measured on a 200k-node swiss roll, K = 8: 100 iterations
+// at m = 8, 27 at m = 16 for a relative residual of 1e-5).
+static int guard_for(const mge_embed_opts& e, int K) {
+  if (e.guard > 0) return e.guard;
+  if (e.guard < 0) return 0;
+  return std::max(0, std::min(K, 24 - K));
+}
+
 // Widths the operator-product entry points support (the SpMM kernel's instantiations).
 static bool apply_width_ok(int m) { return m == 4 || m == 8 || m == 12 || m == 16 || m == 24; }
 
@@ -540,8 +557,9 @@ mge_status mge_embed(mge_ctx* c, const mge_ops* o, int K, double tol, const mge_
   if (e.check_every <= 0) e.check_every = 16;
   if (!(tol > 0)) { set_error(ctx, "tol must be > 0"); return MGE_EINVAL; }
   if (K < 1) { set_error(ctx, "K must be >= 1"); return MGE_EINVAL; }
-  int m = round_block_width(K + std::max(e.guard, 0));
-  if (m < 0 || m > 24) { set_error(ctx, "K + guard = %d exceeds the widest block (24)", K + e.guard); return MGE_EINVAL; }
+  const int guard = guard_for(e, K);
+  int m = round_block_width(K + guard);
+  if (m < 0 || m > 24) { set_error(ctx, "K + guard = %d exceeds the widest block (24)", K + guard); return MGE_EINVAL; }
   const Ops& op = o->impl;
   if (op.n < 2 * m) { set_error(ctx, "graph has %lld nodes; need at least %d", (long long)op.n, 2 * m); return MGE_EINVAL; }
   int prec = e.precision;
@@ -570,6 +588,7 @@ mge_status mge_embed(mge_ctx* c, const mge_ops* o, int K, double tol, const mge_
   }
   LobResult r;
   l.precond_degree = e.precond_degree > 0 ? std::min(e.precond_degree, 64) : kDefaultPrecondDegree;
+  l.rr_fp64 = rr_fp64_for(e, prec);
   mge_status s = lobpcg_solve(ctx, st, l, prec, K, m, tol, e.maxiter, e.seed, e.check_every, e.use_graph != 0,
                               x0, x0c, vout, &r);
   if (s != MGE_OK && s != MGE_ENOTCONVERGED) {
@@ -613,13 +632,15 @@ mge_status mge_embed_batch(mge_ctx* c, int count, const mge_ops* const* ops, con
   for (int i = 0; i < count; ++i) {
     if (!ops[i] || !lambda[i]) { set_error(ctx, "embed_batch: NULL handle or lambda at %d", i); return MGE_EINVAL; }
     if (K[i] < 1) { set_error(ctx, "embed_batch: K[%d] = %d", i, K[i]); return MGE_EINVAL; }
-    const int m = round_block_width(K[i] + std::max(e.guard, 0));
-    if (m < 0 || m > 24) { set_error(ctx, "embed_batch: K + guard = %d exceeds the widest block (24)", K[i] + e.guard); return MGE_EINVAL; }
+    const int guard = guard_for(e, K[i]);
+    const int m = round_block_width(K[i] + guard);
+    if (m < 0 || m > 24) { set_error(ctx, "embed_batch: K + guard = %d exceeds the widest block (24)", K[i] + guard); return MGE_EINVAL; }
     const Ops& op = ops[i]->impl;
     if (op.n < 2 * m) { set_error(ctx, "embed_batch: graph %d has %lld nodes; need at least %d", i, (long long)op.n, 2 * m); return MGE_EINVAL; }
     ms[i] = m;
     lops[i] = make_op(op, 0, prec);
     lops[i].precond_degree = e.precond_degree > 0 ? std::min(e.precond_degree, 64) : kDefaultPrecondDegree;
+    lops[i].rr_fp64 = rr_fp64_for(e, prec);
   }
   cudaStream_t st = pick_stream(ctx, e.stream);
   // V buffers: the caller's device arrays, or scratch copied to the caller's host arrays

@@ -1029,7 +1029,7 @@ struct Solver {
     if (sizeof(T) == 4) { tau = 1e-6; tau_p = 1e-8; tau_w = 1e-4; }
     // the inverse-pencil Rayleigh-Ritz needs G_A positive definite: A = L - mu Q + eps I with
     // eps > 0, or Q with the constant vector deflated
-    inverse_rr = (sizeof(T) == 4) && (op.shift > 0.0 || op.deflate);
+    inverse_rr = (sizeof(T) == 4) && !op.rr_fp64 && (op.shift > 0.0 || op.deflate);
     return MGE_OK;
   }
 
@@ -1244,7 +1244,7 @@ struct Solver {
     w.M = M; w.K = K; w.has_x = hx; w.has_p = hp; w.check = check;
     w.deflate = op.deflate; w.n = n; w.tol = tol; w.norm = op.norm; w.bmax = op.bmax;
     w.tau_w = tau_w; w.maxiter = maxiter; w.st = state;
-    launch_wprep(st, w, sizeof(T) == 8);
+    launch_wprep(st, w, sizeof(T) == 8 || op.rr_fp64);
     MGE_LAUNCHED(ctx, 1);
   }
 

@@ -29,6 +29,19 @@ namespace lob {
 // ---------------------------------------------------------------------------------------
 // shared: sum the cluster partials into gA, gB (FP64, row-major, leading dimension ld)
 // ---------------------------------------------------------------------------------------
+// G_A[i][j] holds s_i^T (A s_j).  Its rounding error is about u times sum_r |s_i[r]| |(A s_j)[r]|,
+// small when A acts on the smoother of the two columns (the smaller Rayleigh quotient,
+// G_A[j][j]): for a Ritz vector x against a rough search direction w, (A x)^T w has terms of
+// size lambda while x^T (A w) has terms of size w's Rayleigh quotient and cancels to the
+// small true value.  So the symmetrised entry takes the product whose A-side column has the
+// smaller diagonal, and averages the two when the diagonals are within a factor of two.
+template <typename R>
+__device__ __forceinline__ R sym_a_entry(R gij, R gji, R gii, R gjj) {
+  if (gjj <= R(0.5) * gii) return gij;
+  if (gii <= R(0.5) * gjj) return gji;
+  return R(0.5) * (gij + gji);
+}
+
 __device__ bool load_grams(const RRArgs& a, double* gA, double* gB, int n, int ld) {
   __shared__ int nonfinite;
   if (threadIdx.x == 0) nonfinite = 0;
@@ -49,7 +62,7 @@ __device__ bool load_grams(const RRArgs& a, double* gA, double* gB, int n, int l
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     int i = t / n, j = t % n;
     if (i < j) {
-      double va = 0.5 * (gA[i * ld + j] + gA[j * ld + i]);
+      double va = sym_a_entry(gA[i * ld + j], gA[j * ld + i], gA[i * ld + i], gA[j * ld + j]);
       gA[i * ld + j] = va; gA[j * ld + i] = va;
       if (i / 4 == j / 4) {
         double vb = 0.5 * (gB[i * ld + j] + gB[j * ld + i]);
@@ -639,7 +652,8 @@ __global__ void __launch_bounds__(kRWThreads) k_rr_warp(RRArgs a) {
     float ga = 0.f, gb = 0.f;
     if (i < n && j < n) {
       const int bi = i / 4, bj = j / 4;
-      ga = 0.5f * ((float)sm->partA[0][i * MAXS + j] + (float)sm->partA[0][j * MAXS + i]);
+      ga = (float)sym_a_entry(sm->partA[0][i * MAXS + j], sm->partA[0][j * MAXS + i],
+                              sm->partA[0][i * MAXS + i], sm->partA[0][j * MAXS + j]);
       const float b1 = (bi <= bj) ? (float)sm->partB[0][i * MAXS + j] : 0.f;
       const float b2 = (bi >= bj) ? (float)sm->partB[0][j * MAXS + i] : 0.f;
       gb = (bi < bj) ? b1 : (bi > bj) ? b2 : 0.5f * (b1 + b2);

@@ -122,7 +122,7 @@ def test_initial_block_is_read_in_the_callers_order(ctx):
     ops = ctx.build(g, precision="fp64")
     assert not np.array_equal(ops.node_order(), np.arange(g.n))
     x0 = np.ascontiguousarray(dense.V[:, :4].T)                # [K, n] = column-major n x K
-    lam, V, info, s = ctx.embed(ops, 4, 1e-8, precision="fp64", guard=0, x0=x0)
+    lam, V, info, s = ctx.embed(ops, 4, 1e-8, precision="fp64", guard=-1, x0=x0)
     assert s == 0
     assert info.iters <= 2, info.iters
     np.testing.assert_allclose(lam, dense.lam[:4], rtol=1e-8)
