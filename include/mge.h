@@ -48,7 +48,9 @@ typedef enum {
   MGE_EISOLATED = 3,      /* some r_i = 0 (isolated node): B is singular (Sec. 4.3)          */
   MGE_EDEGENERATE = 4,    /* eps = lambda_2(Q) = 0: the two-hop graph is disconnected
                              (Sec. 4.2); mu = 0 and A = L.  Outputs are still produced.      */
-  MGE_ENOTCONVERGED = 5,  /* maxiter reached; the current Ritz pairs and residuals returned */
+  MGE_ENOTCONVERGED = 5,  /* maxiter reached, or the iteration stagnated below what its
+                             precision reaches (its basis collapsed after the first
+                             iterations); the current Ritz pairs and residuals returned     */
   MGE_ENOMEM = 6,         /* device allocation failed or the HBM budget is exceeded          */
   MGE_EAGAIN = 7,         /* serving queue or HBM budget full; retry later                   */
   MGE_ETIMEOUT = 8,       /* mge_poll timed out, or a bounded device loop hit its limit      */

@@ -1357,6 +1357,11 @@ struct Solver {
                 mge_strerror(*status), hst->bad_stage, hst->kept);
     } else if (hst->done == DONE_MAXITER || hst->done == DONE_RUNNING) {
       *status = MGE_ENOTCONVERGED;
+    } else if (hst->done == DONE_STALLED) {
+      *status = MGE_ENOTCONVERGED;
+      set_error(ctx, "LOBPCG stagnated at iteration %d (basis of %d directions, fewer than m): the "
+                "tolerance is below what the block precision reaches; current pairs returned",
+                hst->iter, hst->kept);
     }
     if (getenv("MGE_PHASES")) {
       fprintf(stderr, "[mge] n=%lld M=%d iters=%d rr_clk:", (long long)n, M, hst->iter);

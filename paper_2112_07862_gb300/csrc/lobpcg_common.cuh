@@ -17,7 +17,7 @@ constexpr int CL = 8;                // CTAs per cluster in the reducing kernels
 constexpr int MAXCL = 64;            // clusters per reducing launch (grid <= 512 CTAs)
 constexpr int kThreads = 256;
 
-enum : int { DONE_RUNNING = 0, DONE_CONVERGED = 1, DONE_ERROR = 2, DONE_MAXITER = 3 };
+enum : int { DONE_RUNNING = 0, DONE_CONVERGED = 1, DONE_ERROR = 2, DONE_MAXITER = 3, DONE_STALLED = 4 };
 
 struct State {
   int done;

@@ -42,6 +42,13 @@ __device__ __forceinline__ R sym_a_entry(R gij, R gji, R gii, R gjj) {
   return R(0.5) * (gij + gji);
 }
 
+// A basis that collapses (fewer than m independent directions) after the solve has made
+// progress means the iteration has stagnated at its precision's floor: the current pairs
+// stand and the solve ends as not converged.  At the start it is a rank-deficient block.
+__device__ __forceinline__ int stall_or_error(const State* st) {
+  return st->iter >= 2 ? DONE_STALLED : DONE_ERROR;
+}
+
 __device__ bool load_grams(const RRArgs& a, double* gA, double* gB, int n, int ld) {
   __shared__ int nonfinite;
   if (threadIdx.x == 0) nonfinite = 0;
@@ -203,7 +210,7 @@ __global__ void __launch_bounds__(kRRThreads) k_rr_inv(RRArgs a) {
   __syncthreads();
   const int k = kcount;
   if (k < M) {
-    if (threadIdx.x == 0) { a.st->done = DONE_ERROR; a.st->err = MGE_ECHOLESKY; a.st->kept = k; }
+    if (threadIdx.x == 0) { a.st->done = stall_or_error(a.st); a.st->err = MGE_ECHOLESKY; a.st->kept = k; }
     return;
   }
   if (threadIdx.x == 0 && k < n) atomicAdd(&a.st->drops, 1);
@@ -707,7 +714,7 @@ __global__ void __launch_bounds__(kRWThreads) k_rr_warp(RRArgs a) {
   }
   RW_MARK(9);
   if (k < M) {
-    if (threadIdx.x == 0) { a.st->done = DONE_ERROR; a.st->err = MGE_ECHOLESKY; a.st->kept = k; }
+    if (threadIdx.x == 0) { a.st->done = stall_or_error(a.st); a.st->err = MGE_ECHOLESKY; a.st->kept = k; }
     return;
   }
   if (threadIdx.x == 0 && k < n) atomicAdd(&a.st->drops, 1);
@@ -1234,7 +1241,7 @@ __global__ void __launch_bounds__(kThreads) k_rr_jacobi(RRArgs a) {
   __syncthreads();
   const int k = kcount;
   if (k < M) {
-    if (threadIdx.x == 0) { a.st->done = DONE_ERROR; a.st->err = MGE_ECHOLESKY; a.st->kept = k; }
+    if (threadIdx.x == 0) { a.st->done = stall_or_error(a.st); a.st->err = MGE_ECHOLESKY; a.st->kept = k; }
     return;
   }
   if (threadIdx.x == 0 && k < n) atomicAdd(&a.st->drops, 1);

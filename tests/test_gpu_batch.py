@@ -23,7 +23,7 @@ def ctx(gpu_lib):
     c.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-6), ("fp64", 1e-9)])
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp64", 1e-9)])
 def test_batch_equals_alone(ctx, precision, tol):
     graphs = [(mg.manifold_graph(s, n, k, 20 + i), K) for i, (s, n, k, K) in enumerate(GRAPHS)]
     ops = [ctx.build(g, precision=precision) for g, _ in graphs]
@@ -47,7 +47,7 @@ def test_batch_member_matches_dense_oracle(ctx):
     d = oe.dense_geneig(ref.A, ref.b, 5)
     big = mg.manifold_graph("swiss_roll", 6000, 10, 8)
     ops = [ctx.build(big, precision="fp32"), ctx.build(g, precision="fp32")]
-    lams, Vs, infos, s = ctx.embed_batch(ops, [8, 4], 1e-6, precision="fp32", guard=4)
+    lams, Vs, infos, s = ctx.embed_batch(ops, [8, 4], 1e-5, precision="fp32", guard=4)
     assert s == 0
     lam, V = lams[1], Vs[1]
     assert np.max(np.abs(lam - d.lam[:4]) / d.lam[:4]) <= 1e-4

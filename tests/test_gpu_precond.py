@@ -45,7 +45,7 @@ def check(lam, V, ref, dense, K, lam_tol, angle_tol, eta_tol):
 @pytest.mark.parametrize("degree", [1, 4, 24])
 def test_fp32_same_pairs_at_every_degree(ctx, square, degree):
     g, ref, dense, ops = square
-    lam, V, info, s = ctx.embed(ops, 8, 1e-6, precision="fp32", guard=4, precond_degree=degree)
+    lam, V, info, s = ctx.embed(ops, 8, 1e-5, precision="fp32", guard=4, precond_degree=degree)
     assert s == 0
     # the 9th eigenvalue is well separated on this graph, so the first 8 span is defined
     check(lam, V, ref, dense, 8, 1e-4, 2e-3, 2e-6)
@@ -63,7 +63,7 @@ def test_higher_degree_needs_fewer_iterations(ctx, square):
     g, ref, dense, ops = square
     iters = []
     for degree in (1, 8, 24):
-        lam, V, info, s = ctx.embed(ops, 8, 1e-6, precision="fp32", guard=4, precond_degree=degree)
+        lam, V, info, s = ctx.embed(ops, 8, 1e-5, precision="fp32", guard=4, precond_degree=degree)
         assert s == 0
         iters.append(info.iters)
     assert iters[0] > iters[1] > iters[2], iters
@@ -71,7 +71,7 @@ def test_higher_degree_needs_fewer_iterations(ctx, square):
 
 def test_degree_is_clamped_at_64(ctx, square):
     g, ref, dense, ops = square
-    lam, V, info, s = ctx.embed(ops, 4, 1e-6, precision="fp32", guard=4, precond_degree=1000)
+    lam, V, info, s = ctx.embed(ops, 4, 1e-5, precision="fp32", guard=4, precond_degree=1000)
     assert s == 0
     check(lam, V, ref, dense, 4, 1e-4, 2e-3, 2e-6)
 

@@ -10,7 +10,7 @@ import manifold_graphs as mg
 pytestmark = pytest.mark.gpu
 
 
-def request(mge, g, K, tol=1e-6, seed=0, precision="fp32", guard=4):
+def request(mge, g, K, tol=1e-5, seed=0, precision="fp32", guard=4):
     r = mge.mge_request()
     r.n = g.n
     r.row_ptr = g.row_ptr.ctypes.data
@@ -34,7 +34,7 @@ def test_results_are_the_same_alone_and_in_the_mix(gpu_lib):
         alone = []
         for g, K in graphs:
             ops = ctx.build(g, precision="fp32")
-            lam, V, info, s = ctx.embed(ops, K, 1e-6, precision="fp32", guard=4)
+            lam, V, info, s = ctx.embed(ops, K, 1e-5, precision="fp32", guard=4)
             alone.append((lam, V))
             ops.close()
     with mge.Context(0) as ctx:
@@ -91,7 +91,7 @@ def test_eight_slots_every_request_matches_alone(gpu_lib, monkeypatch):
         alone = []
         for g, K in graphs:
             ops = ctx.build(g, precision="fp32")
-            lam, V, info, s = ctx.embed(ops, K, 1e-6, precision="fp32", guard=4)
+            lam, V, info, s = ctx.embed(ops, K, 1e-5, precision="fp32", guard=4)
             alone.append((lam, V))
             ops.close()
     monkeypatch.setenv("MGE_SERVE_SLOTS", "8")
