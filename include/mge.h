@@ -68,7 +68,15 @@ typedef enum {
  *             Rayleigh-Ritz scaling in FP64 and its eigensolve in FP32 on the inverse
  *             pencil (the wanted smallest eigenvalues become the largest, which FP32
  *             resolves to relative accuracy).
- *   MGE_BF16  reserved (rejected with MGE_EINVAL by this build). */
+ *   MGE_BF16  as MGE_FP32, with the LOBPCG preconditioner's blocks -- its right-hand side
+ *             D^-1 R, the Chebyshev iterates and corrections -- stored in BF16 (FP32
+ *             arithmetic in registers; the matrix values stay FP32 so that the Chebyshev
+ *             interval's Gershgorin bound holds).  These blocks are all but a few of the
+ *             bytes a LOBPCG iteration streams.  X, W, P and their products stay FP32: a
+ *             Ritz vector rounded to BF16 carries a residual of about u_bf16 ||A|| |x|, which
+ *             on manifold graphs (||A|| / lambda_1 ~ 1e5-1e6) is far above any useful
+ *             tolerance.  Falls back to FP32 preconditioner blocks when the sliced copy of
+ *             the preconditioner's operator was not built. */
 typedef enum { MGE_FP64 = 0, MGE_FP32 = 1, MGE_BF16 = 2 } mge_precision;
 
 typedef struct mge_ctx mge_ctx;

@@ -562,11 +562,16 @@ mge_status mge_embed(mge_ctx* c, const mge_ops* o, int K, double tol, const mge_
   if (m < 0 || m > 24) { set_error(ctx, "K + guard = %d exceeds the widest block (24)", K + guard); return MGE_EINVAL; }
   const Ops& op = o->impl;
   if (op.n < 2 * m) { set_error(ctx, "graph has %lld nodes; need at least %d", (long long)op.n, 2 * m); return MGE_EINVAL; }
-  int prec = e.precision;
-  if (prec == MGE_BF16) { set_error(ctx, "BF16 blocks are not available in this build"); return MGE_EINVAL; }
-  if (prec != MGE_FP64 && prec != MGE_FP32) { set_error(ctx, "bad precision"); return MGE_EINVAL; }
+  if (e.precision != MGE_FP64 && e.precision != MGE_FP32 && e.precision != MGE_BF16) {
+    set_error(ctx, "bad precision");
+    return MGE_EINVAL;
+  }
+  // MGE_BF16: FP32 blocks and values, the preconditioner's blocks in BF16
+  const bool bf16 = e.precision == MGE_BF16;
+  int prec = bf16 ? MGE_FP32 : e.precision;
   cudaStream_t st = pick_stream(ctx, e.stream);
   LobOp l = make_op(op, 0, prec);
+  l.pc_bf16 = bf16;
   // optional initial block
   DevBuf<double> x0d;
   const double* x0 = nullptr;
@@ -624,9 +629,12 @@ mge_status mge_embed_batch(mge_ctx* c, int count, const mge_ops* const* ops, con
   if (e.maxiter <= 0) e.maxiter = 20000;
   if (!(tol > 0)) { set_error(ctx, "tol must be > 0"); return MGE_EINVAL; }
   if (e.x0 && e.x0_cols > 0) { set_error(ctx, "embed_batch: x0 is not supported"); return MGE_EINVAL; }
-  const int prec = e.precision;
-  if (prec == MGE_BF16) { set_error(ctx, "BF16 blocks are not available in this build"); return MGE_EINVAL; }
-  if (prec != MGE_FP64 && prec != MGE_FP32) { set_error(ctx, "bad precision"); return MGE_EINVAL; }
+  if (e.precision != MGE_FP64 && e.precision != MGE_FP32 && e.precision != MGE_BF16) {
+    set_error(ctx, "bad precision");
+    return MGE_EINVAL;
+  }
+  const bool bf16 = e.precision == MGE_BF16;
+  const int prec = bf16 ? MGE_FP32 : e.precision;
   std::vector<LobOp> lops((size_t)count);
   std::vector<int> ms((size_t)count);
   for (int i = 0; i < count; ++i) {
@@ -641,6 +649,7 @@ mge_status mge_embed_batch(mge_ctx* c, int count, const mge_ops* const* ops, con
     lops[i] = make_op(op, 0, prec);
     lops[i].precond_degree = e.precond_degree > 0 ? std::min(e.precond_degree, 64) : kDefaultPrecondDegree;
     lops[i].rr_fp64 = rr_fp64_for(e, prec);
+    lops[i].pc_bf16 = bf16;
   }
   cudaStream_t st = pick_stream(ctx, e.stream);
   // V buffers: the caller's device arrays, or scratch copied to the caller's host arrays

@@ -61,8 +61,13 @@ __device__ __forceinline__ void ld4i(const int32_t* p, int32_t v[4]) {
   v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
 }
 
-template <typename T, int M>
+template <typename T, typename SB, typename SO, int M>
 __global__ void __launch_bounds__(kChebThreads, sizeof(T) == 4 ? 2 : 1) k_cheb(ChebArgs<T> a, int cap, int nst) {
+  const SB* __restrict__ X = static_cast<const SB*>(a.X);
+  const SB* __restrict__ Rb = static_cast<const SB*>(a.R);
+  const SB* Db = static_cast<const SB*>(a.D);        // may alias Dout: no __restrict__
+  SB* Dout = static_cast<SB*>(a.Dout);
+  SO* __restrict__ Xout = static_cast<SO*>(a.Xout);
   using Sh = ChebShape<M>;
   constexpr int G = Sh::G, GP = Sh::GP, S = Sh::S, TEAM = Sh::TEAM, RPW = Sh::RPW;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -161,7 +166,7 @@ __global__ void __launch_bounds__(kChebThreads, sizeof(T) == 4 ? 2 : 1) k_cheb(C
       const int nit = (nch + S - 1) / S;                                       // per lane
       const int off = (int)(sslp[sl] - tb) + q * 4;
       T acc[4] = {0, 0, 0, 0}, wi[4];
-      ldg4(a.X + row * M + cc, wi);
+      ldg4(X + row * M + cc, wi);
       // chunk c of the row: indices and values at off + 64 c, then the four gathers; two
       // register sets in turn keep the next chunk's gathers in flight while one is summed.
       // With two lanes per row, lane `sub` takes chunks sub, sub + 2, ...; the second lane of
@@ -180,7 +185,7 @@ __global__ void __launch_bounds__(kChebThreads, sizeof(T) == 4 ? 2 : 1) k_cheb(C
             for (int b = 0; b < 4; ++b) v[b] = in ? v[b] : T(0);
           }
 #pragma unroll
-          for (int b = 0; b < 4; ++b) ldg4(a.X + (size_t)j[b] * M + cc, w[b]);
+          for (int b = 0; b < 4; ++b) ldg4(X + (size_t)j[b] * M + cc, w[b]);
         };
         auto consume = [&](const T* v, const T (*w)[4]) {
 #pragma unroll
@@ -208,8 +213,8 @@ __global__ void __launch_bounds__(kChebThreads, sizeof(T) == 4 ? 2 : 1) k_cheb(C
       }
       if (valid && sub == 0) {
         T rr[4], dd[4], dn[4], xn[4];
-        ldg4(a.R + row * M + c0, rr);
-        ld4(a.D + row * M + c0, dd);          // D may be the output array: plain load
+        ldg4(Rb + row * M + c0, rr);
+        ld4(Db + row * M + c0, dd);           // D may be the output array: plain load
         const T dv = __ldg(a.dinv + row);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -218,8 +223,8 @@ __global__ void __launch_bounds__(kChebThreads, sizeof(T) == 4 ? 2 : 1) k_cheb(C
           dn[u] = a.c1 * (a.sd * dd[u]) + a.c2 * z;
           xn[u] = a.sy * wi[u] + dn[u];
         }
-        st4(a.Dout + row * M + c0, dn);
-        st4(a.Xout + row * M + c0, xn);
+        st4(Dout + row * M + c0, dn);
+        st4(Xout + row * M + c0, xn);
       }
     }
     mbar_arrive(&empty[s]);      // this thread is done with stage s (no lane-dependent branch)
@@ -248,12 +253,12 @@ void cheb_config(int64_t max_tile_slots, int* cap, int* nst) {
 
 }  // namespace
 
-template <typename T, int M>
+template <typename T, typename S, typename SO, int M>
 cudaError_t cheb_configure() {
-  return cudaFuncSetAttribute(k_cheb<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChebStageBudget);
+  return cudaFuncSetAttribute(k_cheb<T, S, SO, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChebStageBudget);
 }
 
-template <typename T, int M>
+template <typename T, typename S, typename SO, int M>
 cudaError_t cheb_launch(const Ctx* ctx, cudaStream_t st, const ChebArgs<T>& a, int64_t max_tile_slots) {
   if (a.n <= 0) return cudaSuccess;
   int cap = 0, nst = 0;
@@ -265,30 +270,31 @@ cudaError_t cheb_launch(const Ctx* ctx, cudaStream_t st, const ChebArgs<T>& a, i
   thread_local int per_sm = 1;
   if (smem != last_smem) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb<T, M>, kChebThreads, smem) != cudaSuccess || b < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb<T, S, SO, M>, kChebThreads, smem) != cudaSuccess || b < 1)
       b = 1;
     per_sm = b;
     last_smem = smem;
   }
   const int64_t ntiles = (a.n + kSliceTileRows - 1) / kSliceTileRows;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * per_sm));
-  k_cheb<T, M><<<(unsigned)grid, kChebThreads, smem, st>>>(a, cap, nst);
+  k_cheb<T, S, SO, M><<<(unsigned)grid, kChebThreads, smem, st>>>(a, cap, nst);
   return cudaGetLastError();
 }
 
-#define MGE_CHEB_INST(T, M)                                                                  \
-  template cudaError_t cheb_configure<T, M>();                                               \
-  template cudaError_t cheb_launch<T, M>(const Ctx*, cudaStream_t, const ChebArgs<T>&, int64_t);
-MGE_CHEB_INST(float, 4)
-MGE_CHEB_INST(float, 8)
-MGE_CHEB_INST(float, 12)
-MGE_CHEB_INST(float, 16)
-MGE_CHEB_INST(float, 24)
-MGE_CHEB_INST(double, 4)
-MGE_CHEB_INST(double, 8)
-MGE_CHEB_INST(double, 12)
-MGE_CHEB_INST(double, 16)
-MGE_CHEB_INST(double, 24)
+#define MGE_CHEB_INST(T, S, SO, M)                                                           \
+  template cudaError_t cheb_configure<T, S, SO, M>();                                        \
+  template cudaError_t cheb_launch<T, S, SO, M>(const Ctx*, cudaStream_t, const ChebArgs<T>&, int64_t);
+#define MGE_CHEB_INST_M(M)                                                                   \
+  MGE_CHEB_INST(float, float, float, M)                                                      \
+  MGE_CHEB_INST(double, double, double, M)                                                   \
+  MGE_CHEB_INST(float, __nv_bfloat16, __nv_bfloat16, M)                                      \
+  MGE_CHEB_INST(float, __nv_bfloat16, float, M)
+MGE_CHEB_INST_M(4)
+MGE_CHEB_INST_M(8)
+MGE_CHEB_INST_M(12)
+MGE_CHEB_INST_M(16)
+MGE_CHEB_INST_M(24)
+#undef MGE_CHEB_INST_M
 #undef MGE_CHEB_INST
 
 }  // namespace lob

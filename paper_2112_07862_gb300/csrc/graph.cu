@@ -848,6 +848,7 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
       qop.norm = ops->norm_q; qop.bmax = 1.0; qop.deflate = true; qop.beta = ops->beta_q;
       qop.precond_degree = o.eps_precond_degree > 0 ? std::min(o.eps_precond_degree, 64) : kDefaultEpsPrecondDegree;
       qop.rr_fp64 = true;     // Rayleigh-Ritz in FP64: the relative residual eps needs (see mge_embed)
+      qop.pc_bf16 = o.precision == MGE_BF16;
       if (ops->q_sl.built()) {
         qop.sl_slp = ops->q_sl.slp.p; qop.sl_perm = ops->q_sl.perm.p; qop.sl_col = ops->q_sl.col.p;
         qop.sl_val = (o.precision == MGE_FP64) ? (const void*)ops->q_sl.val.p : (const void*)ops->q_sl.val32.p;

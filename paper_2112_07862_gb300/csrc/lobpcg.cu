@@ -749,6 +749,7 @@ struct UpdArgs {
   const T* b;
   const T* dinv;
   T* Wr;
+  __nv_bfloat16* WrB;        // not NULL: W_raw is stored here in BF16 instead of Wr
   double* partN;             // [ncl][2*MAXM]
   const State* st;
 };
@@ -829,7 +830,12 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads) k_update(
         pr[q] += r[q] * r[q] * ib;
         px[q] += bi * x[q] * x[q];
       }
-      st4(a.Wr + row * M + c0, w);
+      if constexpr (sizeof(T) == 4) {
+        if (a.WrB) st4(a.WrB + row * M + c0, w);
+        else st4(a.Wr + row * M + c0, w);
+      } else {
+        st4(a.Wr + row * M + c0, w);
+      }
     }
     __syncwarp();
   }
@@ -971,6 +977,10 @@ struct Solver {
   int cheb_deg = 1;
   double ch_theta = 1, ch_delta = 1, ch_sigma = 1;
   DevBuf<T> Yc0, Yc1, Dc;
+  // BF16 form: the preconditioner's right-hand side D^-1 R, iterates and corrections in BF16
+  // (its last step writes the preconditioned block to Wr in T)
+  bool pc_bf16 = false;
+  DevBuf<__nv_bfloat16> WrB, Yb0, Yb1, Db;
   const T* wsrc = nullptr;
   std::vector<uint64_t> cap_bytes;     // bytes of the SpMM launches timed inside the graph
   DevBuf<unsigned char> small;
@@ -1001,8 +1011,15 @@ struct Solver {
     MGE_TRY(Wr.scratch(ctx, blk, st));
     wsrc = Wr.p;
     cheb_deg = std::max(1, std::min(op.precond_degree, 64));
+    pc_bf16 = sizeof(T) == 4 && op.pc_bf16 && cheb_deg > 1 && op.sl_slp != nullptr;
+    if (pc_bf16) {
+      MGE_TRY(WrB.scratch(ctx, blk, st)); MGE_TRY(Yb0.scratch(ctx, blk, st));
+      MGE_TRY(Yb1.scratch(ctx, blk, st)); MGE_TRY(Db.scratch(ctx, blk, st));
+    }
     if (cheb_deg > 1) {
-      MGE_TRY(Yc0.scratch(ctx, blk, st)); MGE_TRY(Yc1.scratch(ctx, blk, st)); MGE_TRY(Dc.scratch(ctx, blk, st));
+      if (!pc_bf16) {
+        MGE_TRY(Yc0.scratch(ctx, blk, st)); MGE_TRY(Yc1.scratch(ctx, blk, st)); MGE_TRY(Dc.scratch(ctx, blk, st));
+      }
       // Chebyshev iteration for A y = r on [alpha, beta] of the spectrum of D^-1 A: beta is the
       // Gershgorin bound, alpha = beta / (2 d^2) so that the polynomial reduces the condition
       // number of the preconditioned block by about d^2
@@ -1088,10 +1105,12 @@ struct Solver {
 
   // algorithmic bytes of one Chebyshev step: the operator's indices, values and row
   // pointers, the gathered iterate once, R, d and D^-1 read, d and the next iterate written
-  uint64_t cheb_bytes() const {
-    uint64_t blk = (uint64_t)n * M * sizeof(T);
-    return (uint64_t)nnz_pc * (4 + sizeof(T)) + (uint64_t)(n + 1) * 8 + blk + 2 * blk +
-           (uint64_t)n * sizeof(T) + 2 * blk;
+  // (BF16 form: x, R, d and d_out in 2-byte storage; x_out in T on the last step)
+  uint64_t cheb_bytes(bool last = false) const {
+    const uint64_t s = pc_bf16 ? 2 : sizeof(T), so = (pc_bf16 && !last) ? 2 : sizeof(T);
+    const uint64_t nm = (uint64_t)n * M;
+    return (uint64_t)nnz_pc * (4 + sizeof(T)) + (uint64_t)(n + 1) * 8 + nm * (4 * s + so) +
+           (uint64_t)n * sizeof(T);
   }
 
   // CUDA-event timing of the SpMM launches (ctx->timing): inside a stream capture the
@@ -1163,6 +1182,7 @@ struct Solver {
     // the residual is scaled by the diagonal of the operator the preconditioner applies
     u.dinv = static_cast<const T*>(op.pc_ptr ? op.pc_dinv : op.dinv);
     u.Wr = Wr.p;
+    u.WrB = pc_bf16 ? WrB.p : nullptr;
     u.partN = &sm->partN[0][0];
     u.st = state;
     if (nb == 1) k_update<T, M, 1><<<grid_upd, kThreads, 0, st>>>(u);
@@ -1176,6 +1196,9 @@ struct Solver {
   mge_status launch_cheb(bool timed) {
     wsrc = Wr.p;
     if (cheb_deg <= 1) return MGE_OK;
+    if constexpr (sizeof(T) == 4) {
+      if (pc_bf16) return launch_cheb_bf16(timed);
+    }
     T* ys[2] = {Yc0.p, Yc1.p};
     double rho_prev = 1.0 / ch_sigma;
     for (int k = 1; k < cheb_deg; ++k) {
@@ -1199,7 +1222,7 @@ struct Solver {
         c.c2 = (T)(2.0 * rho / ch_delta);
         c.st = state;
         if (timed) MGE_TRY(time_begin(cheb_bytes()));
-        MGE_CUDA(ctx, (cheb_launch<T, M>(ctx, st, c, op.sl_max_tile_slots)));
+        MGE_CUDA(ctx, (cheb_launch<T, T, T, M>(ctx, st, c, op.sl_max_tile_slots)));
         MGE_LAUNCHED(ctx, 1);
         if (timed) MGE_TRY(time_end());
         rho_prev = rho;
@@ -1234,6 +1257,41 @@ struct Solver {
       rho_prev = rho;
     }
     wsrc = ys[cheb_deg % 2];
+    return MGE_OK;
+  }
+
+  // The same steps with the right-hand side, iterates and corrections in BF16 (written by
+  // k_update and the steps themselves); the last step writes the preconditioned block to Wr.
+  mge_status launch_cheb_bf16(bool timed) {
+    __nv_bfloat16* yb[2] = {Yb0.p, Yb1.p};
+    double rho_prev = 1.0 / ch_sigma;
+    for (int k = 1; k < cheb_deg; ++k) {
+      const double rho = 1.0 / (2.0 * ch_sigma - rho_prev);
+      const bool last = k == cheb_deg - 1;
+      ChebArgs<T> c{};
+      c.n = n;
+      c.slp = op.sl_slp; c.perm = op.sl_perm; c.col = op.sl_col;
+      c.val = static_cast<const T*>(op.sl_val);
+      c.shift = (T)(op.pc_ptr ? op.pc_shift : op.shift);
+      c.X = (k == 1) ? (const void*)WrB.p : (const void*)yb[k % 2];
+      c.R = WrB.p;
+      c.D = (k == 1) ? (const void*)WrB.p : (const void*)Db.p;
+      c.dinv = static_cast<const T*>(op.pc_ptr ? op.pc_dinv : op.dinv);
+      c.Dout = Db.p;
+      c.Xout = last ? (void*)Wr.p : (void*)yb[(k + 1) % 2];
+      c.sy = (k == 1) ? (T)(1.0 / ch_theta) : T(1);
+      c.sd = (k == 1) ? (T)(1.0 / ch_theta) : T(1);
+      c.c1 = (T)(rho * rho_prev);
+      c.c2 = (T)(2.0 * rho / ch_delta);
+      c.st = state;
+      if (timed) MGE_TRY(time_begin(cheb_bytes(last)));
+      if (last) MGE_CUDA(ctx, (cheb_launch<float, __nv_bfloat16, float, M>(ctx, st, c, op.sl_max_tile_slots)));
+      else MGE_CUDA(ctx, (cheb_launch<float, __nv_bfloat16, __nv_bfloat16, M>(ctx, st, c, op.sl_max_tile_slots)));
+      MGE_LAUNCHED(ctx, 1);
+      if (timed) MGE_TRY(time_end());
+      rho_prev = rho;
+    }
+    wsrc = Wr.p;
     return MGE_OK;
   }
 
@@ -1517,7 +1575,13 @@ mge_status prepare_solver(Solver<T, M>& s) {
   }
   MGE_CUDA(ctx, cudaFuncSetAttribute(k_gram<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
   MGE_CUDA(ctx, (spmm_configure<T, M>()));
-  MGE_CUDA(ctx, (cheb_configure<T, M>()));
+  MGE_CUDA(ctx, (cheb_configure<T, T, T, M>()));
+  if constexpr (sizeof(T) == 4) {
+    if (s.pc_bf16) {
+      MGE_CUDA(ctx, (cheb_configure<float, __nv_bfloat16, __nv_bfloat16, M>()));
+      MGE_CUDA(ctx, (cheb_configure<float, __nv_bfloat16, float, M>()));
+    }
+  }
   MGE_CUDA(ctx, rr_configure());
   return MGE_OK;
 }

@@ -84,6 +84,27 @@ __device__ __forceinline__ void ldg4(const double* p, double v[4]) {
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
+// BF16 blocks (4 columns = 8 bytes): widening is exact (a bfloat16 is the top half of a
+// float); narrowing rounds to nearest even
+__device__ __forceinline__ void bf16x4_to_f32(uint2 t, float v[4]) {
+  v[0] = __uint_as_float(t.x << 16); v[1] = __uint_as_float(t.x & 0xffff0000u);
+  v[2] = __uint_as_float(t.y << 16); v[3] = __uint_as_float(t.y & 0xffff0000u);
+}
+__device__ __forceinline__ void ld4(const __nv_bfloat16* p, float v[4]) {
+  bf16x4_to_f32(*reinterpret_cast<const uint2*>(p), v);
+}
+__device__ __forceinline__ void ldg4(const __nv_bfloat16* p, float v[4]) {
+  bf16x4_to_f32(__ldg(reinterpret_cast<const uint2*>(p)), v);
+}
+__device__ __forceinline__ void st4(__nv_bfloat16* p, const float v[4]) {
+  __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+  __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+  uint2 t;
+  t.x = *reinterpret_cast<const uint32_t*>(&a);
+  t.y = *reinterpret_cast<const uint32_t*>(&b);
+  *reinterpret_cast<uint2*>(p) = t;
+}
+
 // Sums `len` doubles that every CTA of the cluster holds at `buf` (shared memory) and stores
 // the cluster total through store(index, value).  Rank r reduces the slice r of the vector,
 // reading all peers' copies through distributed shared memory.
@@ -234,21 +255,23 @@ struct ChebArgs {
   const int32_t* col;
   const T* val;
   T shift;
-  const T* X;
-  const T* R;
-  const T* D;
+  // blocks: T, or bfloat16 storage (S, and SO for x_out) with T = float arithmetic
+  const void* X;
+  const void* R;
+  const void* D;
   const T* dinv;
-  T* Dout;
-  T* Xout;
+  void* Dout;
+  void* Xout;
   T sy, sd, c1, c2;
   State* st;
 };
 
 // Launches the step on stream st; max_tile_slots (the densest tile of the sliced copy) sizes
-// the shared-memory stages.  cheb_configure raises the instances' dynamic shared-memory limit.
-template <typename T, int M>
+// the shared-memory stages.  S is the storage type of x, R, d and d_out, SO that of x_out
+// (T, or __nv_bfloat16 with T = float).  cheb_configure raises the dynamic shared-memory limit.
+template <typename T, typename S, typename SO, int M>
 cudaError_t cheb_launch(const Ctx* ctx, cudaStream_t st, const ChebArgs<T>& a, int64_t max_tile_slots);
-template <typename T, int M>
+template <typename T, typename S, typename SO, int M>
 cudaError_t cheb_configure();
 
 }  // namespace lob

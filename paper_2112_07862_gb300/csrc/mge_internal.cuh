@@ -235,6 +235,7 @@ struct LobOp {
   double beta = 2;                 // upper bound of the spectrum of diag(A)^-1 A
   int precond_degree = 1;          // Chebyshev preconditioner degree (1: Jacobi)
   bool rr_fp64 = false;            // FP32 blocks: Rayleigh-Ritz and W's Cholesky in FP64
+  bool pc_bf16 = false;            // FP32 blocks: the preconditioner's blocks in BF16
   // operator the preconditioner applies, in the same difference form (pc_ptr NULL: the
   // operator itself); its diagonal scaling and Gershgorin bound
   const int64_t* pc_ptr = nullptr;

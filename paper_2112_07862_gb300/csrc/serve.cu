@@ -66,7 +66,7 @@ size_t footprint(const mge_request& r) {
 void run_one(Ctx* ctx, cudaStream_t st, Entry& e) {
   mge_ops* ops = nullptr;
   mge_ops_opts oo{};
-  oo.precision = e.req.precision == MGE_FP64 ? MGE_FP64 : MGE_FP32;
+  oo.precision = (e.req.precision == MGE_FP64 || e.req.precision == MGE_BF16) ? e.req.precision : MGE_FP32;
   oo.seed = e.req.seed;
   oo.stream = st;
   mge_ctx* c = static_cast<mge_ctx*>(ctx->self);

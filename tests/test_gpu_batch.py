@@ -23,7 +23,7 @@ def ctx(gpu_lib):
     c.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp64", 1e-9)])
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("bf16", 1e-5), ("fp64", 1e-9)])
 def test_batch_equals_alone(ctx, precision, tol):
     graphs = [(mg.manifold_graph(s, n, k, 20 + i), K) for i, (s, n, k, K) in enumerate(GRAPHS)]
     ops = [ctx.build(g, precision=precision) for g, _ in graphs]

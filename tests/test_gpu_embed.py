@@ -64,12 +64,15 @@ def test_config_plain_fp64_square_1000(ctx):
 @pytest.mark.parametrize("shape,n,k,K,guard", [("square", 1000, 8, 2, 2), ("square", 1000, 8, 8, 4),
                                                ("swiss_roll", 3000, 10, 8, 4), ("sphere", 2500, 10, 16, 8),
                                                ("torus", 2000, 12, 4, 4)])
-def test_fp32_matches_dense_oracle(ctx, shape, n, k, K, guard):
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_reduced_precision_matches_dense_oracle(ctx, shape, n, k, K, guard, prec):
+    """FP32 blocks, and the BF16 form (the preconditioner's blocks in BF16): the same
+    tolerances against the oracle's dense generalized eigendecomposition."""
     g = mg.manifold_graph(shape, n, k, 3)
     ref = og.from_graph(g)
     d = oe.dense_geneig(ref.A, ref.b, K + 1)
-    ops = ctx.build(g, precision="fp32")
-    lam, V, info, s = ctx.embed(ops, K, 1e-5, precision="fp32", guard=guard)
+    ops = ctx.build(g, precision=prec)
+    lam, V, info, s = ctx.embed(ops, K, 1e-5, precision=prec, guard=guard)
     assert s == 0, s
     compare(lam, V, d.lam, d.V, K, 1e-4)
     VBV = V.T @ (ref.b[:, None] * V)

@@ -1,5 +1,5 @@
-"""The benchmark workload at full size (200,000 swiss-roll points, 10-NN, K = 8, FP32,
-tol 1e-5), checked against the oracle at that size:
+"""The benchmark workload at full size (200,000 swiss-roll points, 10-NN, K = 8, FP32 and
+BF16 forms, relative residual 1e-5), checked against the oracle at that size:
   * the whole A / Q structure and the two-hop counts, bit-exact (oracle sparse build);
   * eps against the oracle's value by shift-invert Lanczos on Q (machine precision, its
     residual asserted), 2e-5 relative: the FP32 eps solve's tolerance;
@@ -54,17 +54,18 @@ def clusters(lam, rel=1e-6):
     return out
 
 
-def test_config_swiss_roll_200k_fp32(gpu_lib):
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_config_swiss_roll_200k(gpu_lib, prec):
     K = 8
     ref_s, ref_V = _reference("swiss_roll_200k")
     assert ref_s["eps_residual"] < 1e-12          # the eps reference converged
     assert max(ref_s["eta"]) < 1e-12              # and so did its eigenpairs
     g = mg.manifold_graph("swiss_roll", 200_000, 10, 2)
     with gpu_lib.Context(0) as ctx:
-        ops = ctx.build(g, precision="fp32")
+        ops = ctx.build(g, precision=prec)
         info = ops.info()
         ex = ops.export()
-        lam, V, ei, s = ctx.embed(ops, K, 1e-5, precision="fp32")
+        lam, V, ei, s = ctx.embed(ops, K, 1e-5, precision=prec)
         ops.close()
     assert s == 0
     assert np.all(np.asarray(ei.resid[:K]) <= 1e-5)     # the solver's own relative residual
