@@ -76,7 +76,14 @@ typedef enum {
  *             Ritz vector rounded to BF16 carries a residual of about u_bf16 ||A|| |x|, which
  *             on manifold graphs (||A|| / lambda_1 ~ 1e5-1e6) is far above any useful
  *             tolerance.  Falls back to FP32 preconditioner blocks when the sliced copy of
- *             the preconditioner's operator was not built. */
+ *             the preconditioner's operator was not built.  The preconditioner degree is
+ *             capped at 8: the Chebyshev polynomial scales the bottom of the spectrum by
+ *             about 2 d^2 against the top, and BF16 rounding of its iterates (u = 2^-8)
+ *             spoils the directions LOBPCG needs once u 2 d^2 > 1.  Measured on a 200k-node
+ *             swiss roll (K = 8, tol 1e-5): no faster per Chebyshev step than FP32 (the step
+ *             is bound by gather latency, not bytes) and more iterations, so MGE_FP32 is the
+ *             faster form on this path; MGE_BF16 is kept for callers that must halve the
+ *             preconditioner's memory. */
 typedef enum { MGE_FP64 = 0, MGE_FP32 = 1, MGE_BF16 = 2 } mge_precision;
 
 typedef struct mge_ctx mge_ctx;

@@ -849,6 +849,7 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
       qop.precond_degree = o.eps_precond_degree > 0 ? std::min(o.eps_precond_degree, 64) : kDefaultEpsPrecondDegree;
       qop.rr_fp64 = true;     // Rayleigh-Ritz in FP64: the relative residual eps needs (see mge_embed)
       qop.pc_bf16 = o.precision == MGE_BF16;
+      if (qop.pc_bf16) qop.precond_degree = std::min(qop.precond_degree, kBf16MaxPrecondDegree);
       if (ops->q_sl.built()) {
         qop.sl_slp = ops->q_sl.slp.p; qop.sl_perm = ops->q_sl.perm.p; qop.sl_col = ops->q_sl.col.p;
         qop.sl_val = (o.precision == MGE_FP64) ? (const void*)ops->q_sl.val.p : (const void*)ops->q_sl.val32.p;

@@ -221,6 +221,12 @@ struct Ops {
 // embedding and from 24 to 32 for the eps solve)
 constexpr int kDefaultPrecondDegree = 48;
 constexpr int kDefaultEpsPrecondDegree = 24;
+// BF16 preconditioner blocks: the Chebyshev polynomial amplifies the bottom of the spectrum by
+// about 2 d^2 against the top, so BF16 rounding (u = 2^-8) of its iterates leaves the
+// preconditioned block with an O(1) relative error in the directions LOBPCG needs once
+// u 2 d^2 > 1 (measured on a 200k-node swiss roll: d >= 24 stalls at eigenvalue errors of
+// 7e-5).  The degree is capped where u 2 d^2 = 1/2.
+constexpr int kBf16MaxPrecondDegree = 8;
 
 struct LobOp {
   int64_t n = 0;
