@@ -112,6 +112,39 @@ mge_status mge_ctx_stats(const mge_ctx* ctx, mge_stats* out);
 mge_status mge_ctx_set_timing(mge_ctx* ctx, int on);
 mge_status mge_ctx_reset_stats(mge_ctx* ctx);
 
+/* ---- kNN graph from points (Sec. 5.1) ---------------------------------------------- */
+
+/* The paper's input graphs are kNN graphs built from Euclidean distances between samples
+ * (Sec. 5.1).  mge_knn_graph builds one on the device:
+ *   - the exact k nearest neighbours of every point (itself excluded); the squared distance
+ *     is the sum over coordinates, in order, of (p_c - q_c)^2 with every product and sum
+ *     rounded to FP64 separately (no fused multiply-add); equal distances go to the lower
+ *     index;
+ *   - the union of the directed relations (i ~ j when either is among the other's k nearest);
+ *   - Gaussian weights w_ij = exp(-d_ij^2 / sigma^2), sigma the mean of the n k directed
+ *     nearest-neighbour distances.
+ * The result is canonical CSR (ascending columns, no diagonal, symmetric), ready for
+ * mge_build_graph_ops with on_device = 1 (see mge_graph_csr).
+ * points: row-major [n x dim] FP64, host or device per on_device (a device pointer of the
+ * context's device, 16-byte aligned), read only.
+ * dim in {2, 3}; 1 <= k <= 32; k < n < 2^31.  stream: cudaStream_t or NULL.
+ * Errors: MGE_EINVAL (sizes; non-finite coordinates; all points coincident; a row with more
+ * than 1024 candidate neighbours, which only many coincident points produce), MGE_ENOMEM,
+ * MGE_EDEVICE. */
+typedef struct mge_graph mge_graph;
+mge_status mge_knn_graph(mge_ctx* ctx, int64_t n, int dim, const double* points, int on_device, int k,
+                         void* stream, mge_graph** out);
+/* n, nnz (directed entries of the CSR) and sigma of a graph; any pointer may be NULL. */
+mge_status mge_graph_info(const mge_graph* g, int64_t* n, int64_t* nnz, double* sigma);
+/* The device arrays of the graph (row_ptr [n+1], col [nnz], w [nnz]), borrowed: valid until
+ * mge_graph_destroy.  Pass them to mge_build_graph_ops with on_device = 1. */
+mge_status mge_graph_csr(const mge_graph* g, const int64_t** row_ptr, const int32_t** col,
+                         const double** w);
+/* Copies the CSR out; any pointer may be NULL; on_device selects device or host destinations. */
+mge_status mge_graph_export(const mge_graph* g, int64_t* row_ptr, int32_t* col, double* w,
+                            int on_device);
+mge_status mge_graph_destroy(mge_graph* g);
+
 /* ---- graph operators (Sec. 3.1, Sec. 4.1-4.3) --------------------------------------- */
 
 typedef struct {

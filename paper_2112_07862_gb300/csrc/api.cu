@@ -457,6 +457,92 @@ mge_status mge_ops_node_order(const mge_ops* o, int32_t* order, int on_device) {
   return MGE_OK;
 }
 
+// ---- kNN graph from points -------------------------------------------------------------
+
+mge_status mge_knn_graph(mge_ctx* c, int64_t n, int dim, const double* points, int on_device, int k,
+                         void* stream, mge_graph** out) {
+  if (!c || !out || !points) return MGE_EINVAL;
+  *out = nullptr;
+  Ctx* ctx = &c->impl;
+  if (ctx->closed) return MGE_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return MGE_EDEVICE;
+  if (n < 2 || dim < 2 || dim > 3 || k < 1 || k > 32 || k >= n) {
+    set_error(ctx, "knn_graph: need dim in {2, 3}, 1 <= k <= 32 and k < n");
+    return MGE_EINVAL;
+  }
+  cudaStream_t st = pick_stream(ctx, stream);
+  if (on_device) MGE_TRY(check_block_ptr(ctx, points, "knn_graph", "points"));
+  mge_graph* g = new mge_graph();
+  g->impl.ctx = ctx;
+  ctx->refs++;
+  mge_status s;
+  {
+    PersistentPoolScope pool_scope(st);      // the graph's arrays come from the context's pool
+    DevBuf<double> pd;
+    const double* P = points;
+    s = MGE_OK;
+    if (!on_device) {
+      s = pd.scratch(ctx, (size_t)n * dim, st);
+      if (s == MGE_OK) {
+        cudaError_t e = cudaMemcpyAsync(pd.p, points, (size_t)n * dim * sizeof(double), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) { set_error(ctx, "knn_graph: copy of the points: %s", cudaGetErrorString(e)); s = MGE_EDEVICE; }
+      }
+      P = pd.p;
+    }
+    if (s == MGE_OK) s = knn_graph_build(ctx, st, n, dim, P, k, &g->impl);
+    if (s == MGE_OK && cudaStreamSynchronize(st) != cudaSuccess) s = MGE_EDEVICE;
+  }
+  if (s != MGE_OK) {
+    g->impl.each_buffer([](auto& b) { if (b.pooled) b.st = cudaStreamPerThread; });
+    delete g;
+    ctx_release(ctx);
+    return s;
+  }
+  *out = g;
+  return MGE_OK;
+}
+
+mge_status mge_graph_info(const mge_graph* g, int64_t* n, int64_t* nnz, double* sigma) {
+  if (!g) return MGE_EINVAL;
+  if (n) *n = g->impl.n;
+  if (nnz) *nnz = g->impl.nnz;
+  if (sigma) *sigma = g->impl.sigma;
+  return MGE_OK;
+}
+
+mge_status mge_graph_csr(const mge_graph* g, const int64_t** row_ptr, const int32_t** col, const double** w) {
+  if (!g) return MGE_EINVAL;
+  if (row_ptr) *row_ptr = g->impl.row_ptr.p;
+  if (col) *col = g->impl.col.p;
+  if (w) *w = g->impl.w.p;
+  return MGE_OK;
+}
+
+mge_status mge_graph_export(const mge_graph* g, int64_t* row_ptr, int32_t* col, double* w, int on_device) {
+  if (!g) return MGE_EINVAL;
+  const Graph& gr = g->impl;
+  Ctx* ctx = gr.ctx;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->closed ? nullptr : ctx->stream;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (row_ptr) MGE_CUDA(ctx, cudaMemcpyAsync(row_ptr, gr.row_ptr.p, (gr.n + 1) * sizeof(int64_t), kind, st));
+  if (col) MGE_CUDA(ctx, cudaMemcpyAsync(col, gr.col.p, gr.nnz * sizeof(int32_t), kind, st));
+  if (w) MGE_CUDA(ctx, cudaMemcpyAsync(w, gr.w.p, gr.nnz * sizeof(double), kind, st));
+  MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  return MGE_OK;
+}
+
+mge_status mge_graph_destroy(mge_graph* g) {
+  if (!g) return MGE_EINVAL;
+  Ctx* ctx = g->impl.ctx;
+  if (ctx) cudaSetDevice(ctx->device);
+  // as mge_ops_destroy: the pooled arrays go back on this thread's per-thread default stream
+  g->impl.each_buffer([](auto& b) { if (b.pooled) b.st = cudaStreamPerThread; });
+  delete g;
+  if (ctx) ctx_release(ctx);
+  return MGE_OK;
+}
+
 static LobOp make_op(const Ops& op, int which, int precision) {
   LobOp l;
   l.n = op.n;

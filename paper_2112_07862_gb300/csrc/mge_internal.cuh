@@ -214,6 +214,24 @@ struct Ops {
 };
 
 // ---------------------------------------------------------------------------------------
+// kNN graph built from points by mge_knn_graph (device resident, canonical CSR)
+// ---------------------------------------------------------------------------------------
+struct Graph {
+  Ctx* ctx = nullptr;
+  int64_t n = 0, nnz = 0;
+  int dim = 0, k = 0;
+  double sigma = 0, cell_size = 0;
+  DevBuf<int64_t> row_ptr;
+  DevBuf<int32_t> col;
+  DevBuf<double> w;
+  template <typename F>
+  void each_buffer(F f) { f(row_ptr); f(col); f(w); }
+};
+
+// Builds the symmetric kNN graph of n points (row-major n x dim FP64, device) into out (knn.cu).
+mge_status knn_graph_build(Ctx* ctx, cudaStream_t st, int64_t n, int dim, const double* P, int k, Graph* out);
+
+// ---------------------------------------------------------------------------------------
 // LOBPCG operator description handed to the solver
 // ---------------------------------------------------------------------------------------
 // default degrees of the Chebyshev preconditioner of the LOBPCG solves (measured on a
@@ -313,3 +331,4 @@ inline int ceil_div_i(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 struct mge_ctx { mge::Ctx impl; };
 struct mge_ops { mge::Ops impl; };
+struct mge_graph { mge::Graph impl; };

@@ -26,7 +26,7 @@ EXPORTS = [
     "mge_create", "mge_destroy", "mge_strerror", "mge_ctx_last_error", "mge_ctx_stats",
     "mge_ctx_set_timing", "mge_ctx_reset_stats", "mge_build_graph_ops", "mge_build_graph_ops_batch", "mge_ops_destroy",
     "mge_ops_info", "mge_ops_export", "mge_ops_node_order", "mge_ops_apply", "mge_ops_apply_inplace", "mge_embed", "mge_embed_batch", "mge_submit", "mge_poll",
-    "mge_release",
+    "mge_release", "mge_knn_graph", "mge_graph_info", "mge_graph_csr", "mge_graph_export", "mge_graph_destroy",
 ]
 
 
@@ -106,6 +106,11 @@ def load(path: str = LIB_PATH):
         "mge_submit": (i, [vp, C.POINTER(mge_request), C.POINTER(u64)]),
         "mge_poll": (i, [vp, u64, i, C.POINTER(mge_result)]),
         "mge_release": (i, [vp, u64]),
+        "mge_knn_graph": (i, [vp, i64, i, vp, i, i, vp, C.POINTER(vp)]),
+        "mge_graph_info": (i, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(d)]),
+        "mge_graph_csr": (i, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
+        "mge_graph_export": (i, [vp, vp, vp, vp, i]),
+        "mge_graph_destroy": (i, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -184,6 +189,52 @@ def mge_build_graph_ops(ctx, n, row_ptr, col, w, on_device: bool = False, opts: 
                                    C.byref(opts) if opts is not None else None, C.byref(h))
     _check(ctx, s, "mge_build_graph_ops", ok=(MGE_OK, MGE_EDEGENERATE))
     return h, s
+
+
+def mge_knn_graph(ctx, points, k: int, stream=None):
+    """kNN graph of the points (numpy [n, dim] float64 on the host, or a torch CUDA tensor).
+    Returns the graph handle."""
+    on_device = hasattr(points, "data_ptr")
+    if not on_device:
+        points = np.ascontiguousarray(points, dtype=np.float64)
+    n, dim = int(points.shape[0]), int(points.shape[1])
+    h = C.c_void_p()
+    s = load().mge_knn_graph(ctx, n, dim, _ptr(points), 1 if on_device else 0, int(k), stream, C.byref(h))
+    _check(ctx, s, "mge_knn_graph")
+    return h
+
+
+def mge_graph_info(g):
+    n, nnz, sigma = C.c_int64(), C.c_int64(), C.c_double()
+    s = load().mge_graph_info(g, C.byref(n), C.byref(nnz), C.byref(sigma))
+    if s != MGE_OK:
+        raise MgeError(s, "mge_graph_info")
+    return n.value, nnz.value, sigma.value
+
+
+def mge_graph_csr(g):
+    """Borrowed device pointers (row_ptr, col, w) of the graph."""
+    rp, col, w = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    s = load().mge_graph_csr(g, C.byref(rp), C.byref(col), C.byref(w))
+    if s != MGE_OK:
+        raise MgeError(s, "mge_graph_csr")
+    return rp.value, col.value, w.value
+
+
+def mge_graph_export(g):
+    """Host copies (row_ptr int64, col int32, w float64) of the graph's CSR."""
+    n, nnz, _ = mge_graph_info(g)
+    rp = np.empty(n + 1, np.int64)
+    col = np.empty(nnz, np.int32)
+    w = np.empty(nnz, np.float64)
+    s = load().mge_graph_export(g, _ptr(rp), _ptr(col), _ptr(w), 0)
+    if s != MGE_OK:
+        raise MgeError(s, "mge_graph_export")
+    return rp, col, w
+
+
+def mge_graph_destroy(g) -> int:
+    return load().mge_graph_destroy(g)
 
 
 def mge_build_graph_ops_batch(ctx, graphs, on_device: bool = False, opts: mge_ops_opts | None = None,
