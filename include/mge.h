@@ -354,6 +354,27 @@ mge_status mge_embed_batch(mge_ctx* ctx, int count, const mge_ops* const* ops, c
                            double tol, const mge_embed_opts* opts, double* const* lambda,
                            void* const* V, mge_embed_info* info);
 
+/* ---- k-means of the embedding (Sec. 5.2) ------------------------------------------- */
+
+/* The paper clusters its embeddings with kmeans (Sec. 5.2, Table 3).  Lloyd's algorithm in
+ * FP64 from the caller's initial centres (random choices are the caller's):
+ *   assignment  each point to the centre of least squared distance, the squared distance
+ *               summed over coordinates in order with each product and sum rounded
+ *               separately (no fused multiply-add); equal distances go to the lower index;
+ *   update      each centre becomes the mean of its points (each coordinate's sum rounded
+ *               once from a compensated double-double, divided by the count); a centre
+ *               without points stays;
+ *   stop        after an assignment step other than the first that changed nothing, or
+ *               after max_iters assignment steps.
+ * X: column-major [n x K] FP64 (the layout mge_embed returns V in).  centres0: row-major
+ * [C x K].  assign [n] int32 and centres [C x K] (row-major) are written; *iters receives
+ * the assignment steps taken.  All pointers host or device per on_device (device pointers
+ * 16-byte aligned).  1 <= K <= 64, C >= 1, C K <= 4096.  Errors: MGE_EINVAL, MGE_ENOMEM,
+ * MGE_EDEVICE. */
+mge_status mge_kmeans(mge_ctx* ctx, int64_t n, int K, const double* X, int C, const double* centres0,
+                      int max_iters, int on_device, int32_t* assign, double* centres, int* iters,
+                      void* stream);
+
 /* ---- serving: continuous batching of embedding requests ---------------------------- */
 
 typedef struct {
@@ -367,6 +388,12 @@ typedef struct {
   int            guard;
   int            maxiter;
   uint64_t       seed;
+  /* Alternatively the request is given as points (row_ptr, col, w unused): host row-major
+   * [n x dim] FP64, copied at submit; the serving slot builds their kNN graph with knn
+   * neighbours on the device (mge_knn_graph, Sec. 5.1) before the operators.            */
+  const double*  points;
+  int            dim;
+  int            knn;
 } mge_request;
 
 typedef struct {

@@ -543,6 +543,48 @@ mge_status mge_graph_destroy(mge_graph* g) {
   return MGE_OK;
 }
 
+// ---- k-means of the embedding --------------------------------------------------------------
+
+mge_status mge_kmeans(mge_ctx* c, int64_t n, int K, const double* X, int C, const double* centres0, int max_iters,
+                      int on_device, int32_t* assign, double* centres, int* iters, void* stream) {
+  if (!c || !X || !centres0 || !assign || !centres) return MGE_EINVAL;
+  Ctx* ctx = &c->impl;
+  if (ctx->closed) return MGE_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return MGE_EDEVICE;
+  if (n < 1 || K < 1 || K > 64 || C < 1 || (int64_t)C * K > 4096 || max_iters < 1) {
+    set_error(ctx, "kmeans: need n >= 1, 1 <= K <= 64, C >= 1, C K <= 4096, max_iters >= 1");
+    return MGE_EINVAL;
+  }
+  cudaStream_t st = pick_stream(ctx, stream);
+  const size_t cb = (size_t)C * K * sizeof(double);
+  DevBuf<double> xd, cd;
+  DevBuf<int32_t> ad;
+  const double* Xd = X;
+  double* Cd = centres;
+  int32_t* Ad = assign;
+  if (on_device) {
+    for (const void* p : {(const void*)X, (const void*)centres0, (const void*)assign, (const void*)centres})
+      MGE_TRY(check_block_ptr(ctx, p, "kmeans", "a buffer"));
+    if (centres != centres0) MGE_CUDA(ctx, cudaMemcpyAsync(centres, centres0, cb, cudaMemcpyDeviceToDevice, st));
+  } else {
+    MGE_TRY(xd.scratch(ctx, (size_t)n * K, st));
+    MGE_TRY(cd.scratch(ctx, (size_t)C * K, st));
+    MGE_TRY(ad.scratch(ctx, (size_t)n, st));
+    MGE_CUDA(ctx, cudaMemcpyAsync(xd.p, X, (size_t)n * K * sizeof(double), cudaMemcpyHostToDevice, st));
+    MGE_CUDA(ctx, cudaMemcpyAsync(cd.p, centres0, cb, cudaMemcpyHostToDevice, st));
+    Xd = xd.p; Cd = cd.p; Ad = ad.p;
+  }
+  int steps = 0;
+  MGE_TRY(kmeans_run(ctx, st, n, K, Xd, C, Cd, max_iters, Ad, &steps));
+  if (!on_device) {
+    MGE_CUDA(ctx, cudaMemcpyAsync(assign, ad.p, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MGE_CUDA(ctx, cudaMemcpyAsync(centres, cd.p, cb, cudaMemcpyDeviceToHost, st));
+  }
+  MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  if (iters) *iters = steps;
+  return MGE_OK;
+}
+
 static LobOp make_op(const Ops& op, int which, int precision) {
   LobOp l;
   l.n = op.n;

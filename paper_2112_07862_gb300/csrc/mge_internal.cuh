@@ -231,6 +231,11 @@ struct Graph {
 // Builds the symmetric kNN graph of n points (row-major n x dim FP64, device) into out (knn.cu).
 mge_status knn_graph_build(Ctx* ctx, cudaStream_t st, int64_t n, int dim, const double* P, int k, Graph* out);
 
+// k-means (Lloyd) of n points (X column-major [n x K], device) from the centres (row-major
+// [C x K], device, updated in place); assign [n] device; kmeans.cu.
+mge_status kmeans_run(Ctx* ctx, cudaStream_t st, int64_t n, int K, const double* X, int C, double* centres,
+                      int max_iters, int32_t* assign, int* iters_out);
+
 // ---------------------------------------------------------------------------------------
 // LOBPCG operator description handed to the solver
 // ---------------------------------------------------------------------------------------

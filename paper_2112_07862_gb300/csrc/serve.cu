@@ -24,6 +24,7 @@ struct Entry {
   std::vector<int64_t> rp;
   std::vector<int32_t> col;
   std::vector<double> w;
+  std::vector<double> points;  // a request given as points: its kNN graph is built on the device
   size_t footprint = 0;
   Clock::time_point t_submit, t_admit, t_done;
   bool done = false;
@@ -50,12 +51,15 @@ struct Serve {
 // FP32 values), and the seven LOBPCG blocks of its FP32 or FP64 iteration.
 size_t footprint(const mge_request& r) {
   int64_t n = r.n;
-  int64_t nnz = r.row_ptr ? r.row_ptr[r.n] : 0;
+  // a request given as points: the union kNN graph holds between k and about 1.5 k entries
+  // per row; the kNN construction's own scratch is below the build's
+  int64_t nnz = r.points ? (int64_t)(1.5 * r.knn * n) : (r.row_ptr ? r.row_ptr[r.n] : 0);
   double deg = n > 0 ? (double)nnz / n : 0;
   double cand = (double)nnz * deg;                 // sum of candidate counts
   double nnz_t = std::min(cand, (double)nnz * 2.5);
   double nnz_a = n + nnz + nnz_t, nnz_q = n + nnz_t;
-  int m = round_block_width(r.K + std::max(r.guard, 0));
+  const int guard = r.guard > 0 ? r.guard : r.guard < 0 ? 0 : std::max(0, std::min(r.K, 24 - r.K));
+  int m = round_block_width(r.K + guard);
   if (m < 0) m = 24;
   size_t es = r.precision == MGE_FP64 ? 8 : 4;
   double bytes = nnz * 12.0 + cand * 4.0 + nnz_a * 16.0 + nnz_q * 16.0 + n * 80.0 +
@@ -70,7 +74,21 @@ void run_one(Ctx* ctx, cudaStream_t st, Entry& e) {
   oo.seed = e.req.seed;
   oo.stream = st;
   mge_ctx* c = static_cast<mge_ctx*>(ctx->self);
-  mge_status s = mge_build_graph_ops(c, e.req.n, e.rp.data(), e.col.data(), e.w.data(), 0, &oo, &ops);
+  mge_status s;
+  if (!e.points.empty()) {
+    // points -> kNN graph (Sec. 5.1) -> operators, all on the slot's stream
+    mge_graph* g = nullptr;
+    s = mge_knn_graph(c, e.req.n, e.req.dim, e.points.data(), 0, e.req.knn, st, &g);
+    if (s != MGE_OK) { e.status = s; return; }
+    const int64_t* rp = nullptr;
+    const int32_t* col = nullptr;
+    const double* w = nullptr;
+    mge_graph_csr(g, &rp, &col, &w);
+    s = mge_build_graph_ops(c, e.req.n, rp, col, w, 1, &oo, &ops);
+    mge_graph_destroy(g);
+  } else {
+    s = mge_build_graph_ops(c, e.req.n, e.rp.data(), e.col.data(), e.w.data(), 0, &oo, &ops);
+  }
   if (s != MGE_OK && s != MGE_EDEGENERATE) { e.status = s; return; }
   mge_ops_info_t info{};
   mge_ops_info(ops, &info);
@@ -147,18 +165,25 @@ Serve* get_serve(Ctx* ctx) {
 }  // namespace
 
 mge_status serve_submit(Ctx* ctx, const mge_request* req, uint64_t* ticket) {
-  if (req->n < 1 || !req->row_ptr || !req->col || !req->w || req->K < 1 || !(req->tol > 0)) {
+  const bool pts = req->points != nullptr;
+  if (req->n < 1 || req->K < 1 || !(req->tol > 0) ||
+      (pts && (req->dim < 2 || req->dim > 3 || req->knn < 1 || req->knn > 32 || req->knn >= req->n)) ||
+      (!pts && (!req->row_ptr || !req->col || !req->w))) {
     set_error(ctx, "submit: invalid request");
     return MGE_EINVAL;
   }
   Serve* sv = get_serve(ctx);
   Entry e;
   e.req = *req;
-  int64_t nnz = req->row_ptr[req->n];
-  if (nnz < 0) { set_error(ctx, "submit: bad row_ptr"); return MGE_EINVAL; }
-  e.rp.assign(req->row_ptr, req->row_ptr + req->n + 1);
-  e.col.assign(req->col, req->col + nnz);
-  e.w.assign(req->w, req->w + nnz);
+  if (pts) {
+    e.points.assign(req->points, req->points + (size_t)req->n * req->dim);
+  } else {
+    int64_t nnz = req->row_ptr[req->n];
+    if (nnz < 0) { set_error(ctx, "submit: bad row_ptr"); return MGE_EINVAL; }
+    e.rp.assign(req->row_ptr, req->row_ptr + req->n + 1);
+    e.col.assign(req->col, req->col + nnz);
+    e.w.assign(req->w, req->w + nnz);
+  }
   e.footprint = footprint(*req);
   e.t_submit = Clock::now();
   {
@@ -169,7 +194,7 @@ mge_status serve_submit(Ctx* ctx, const mge_request* req, uint64_t* ticket) {
     }
     if (sv->queue.size() >= sv->max_queue) return MGE_EAGAIN;
     uint64_t t = sv->next_ticket++;
-    e.req.row_ptr = nullptr; e.req.col = nullptr; e.req.w = nullptr;
+    e.req.row_ptr = nullptr; e.req.col = nullptr; e.req.w = nullptr; e.req.points = nullptr;
     sv->entries.emplace(t, std::move(e));
     sv->queue.push_back(t);
     *ticket = t;

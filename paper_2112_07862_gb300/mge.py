@@ -26,7 +26,7 @@ EXPORTS = [
     "mge_create", "mge_destroy", "mge_strerror", "mge_ctx_last_error", "mge_ctx_stats",
     "mge_ctx_set_timing", "mge_ctx_reset_stats", "mge_build_graph_ops", "mge_build_graph_ops_batch", "mge_ops_destroy",
     "mge_ops_info", "mge_ops_export", "mge_ops_node_order", "mge_ops_apply", "mge_ops_apply_inplace", "mge_embed", "mge_embed_batch", "mge_submit", "mge_poll",
-    "mge_release", "mge_knn_graph", "mge_graph_info", "mge_graph_csr", "mge_graph_export", "mge_graph_destroy",
+    "mge_release", "mge_kmeans", "mge_knn_graph", "mge_graph_info", "mge_graph_csr", "mge_graph_export", "mge_graph_destroy",
 ]
 
 
@@ -64,7 +64,8 @@ class mge_embed_info(C.Structure):
 class mge_request(C.Structure):
     _fields_ = [("n", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("w", C.c_void_p),
                 ("K", C.c_int), ("tol", C.c_double), ("precision", C.c_int), ("guard", C.c_int),
-                ("maxiter", C.c_int), ("seed", C.c_uint64)]
+                ("maxiter", C.c_int), ("seed", C.c_uint64), ("points", C.c_void_p), ("dim", C.c_int),
+                ("knn", C.c_int)]
 
 
 class mge_result(C.Structure):
@@ -107,6 +108,7 @@ def load(path: str = LIB_PATH):
         "mge_poll": (i, [vp, u64, i, C.POINTER(mge_result)]),
         "mge_release": (i, [vp, u64]),
         "mge_knn_graph": (i, [vp, i64, i, vp, i, i, vp, C.POINTER(vp)]),
+        "mge_kmeans": (i, [vp, i64, i, vp, i, vp, i, i, vp, vp, C.POINTER(i), vp]),
         "mge_graph_info": (i, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(d)]),
         "mge_graph_csr": (i, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
         "mge_graph_export": (i, [vp, vp, vp, vp, i]),
@@ -127,9 +129,11 @@ class MgeError(RuntimeError):
 
 
 def _ptr(a):
-    """Host numpy array or torch tensor -> address (None passes NULL)."""
+    """Host numpy array, torch tensor or raw address (int) -> address (None passes NULL)."""
     if a is None:
         return None
+    if isinstance(a, int):
+        return a
     if hasattr(a, "data_ptr"):
         return a.data_ptr()
     return a.ctypes.data
@@ -202,6 +206,32 @@ def mge_knn_graph(ctx, points, k: int, stream=None):
     s = load().mge_knn_graph(ctx, n, dim, _ptr(points), 1 if on_device else 0, int(k), stream, C.byref(h))
     _check(ctx, s, "mge_knn_graph")
     return h
+
+
+def mge_kmeans(ctx, X, centres0, max_iters: int, stream=None):
+    """k-means of the rows of X (numpy [n, K] float64, or a torch CUDA tensor [K, n] -- the
+    column-major layout mge_embed returns V in) from centres0 [C, K].  Returns (assign int32
+    [n], centres [C, K], assignment steps) as numpy arrays on the host path, torch tensors on
+    the device path."""
+    iters = C.c_int()
+    if hasattr(X, "data_ptr"):
+        import torch
+        K, n = int(X.shape[0]), int(X.shape[1])
+        c0 = centres0.contiguous()
+        a = torch.empty(n, dtype=torch.int32, device=X.device)
+        cen = torch.empty_like(c0)
+        s = load().mge_kmeans(ctx, n, K, _ptr(X), int(c0.shape[0]), _ptr(c0), int(max_iters), 1, _ptr(a),
+                              _ptr(cen), C.byref(iters), stream)
+    else:
+        Xc = np.asfortranarray(X, dtype=np.float64)             # column-major [n x K]
+        n, K = Xc.shape
+        c0 = np.ascontiguousarray(centres0, dtype=np.float64)
+        a = np.empty(n, np.int32)
+        cen = np.empty_like(c0)
+        s = load().mge_kmeans(ctx, n, K, Xc.ctypes.data, int(c0.shape[0]), _ptr(c0), int(max_iters), 0, _ptr(a),
+                              _ptr(cen), C.byref(iters), stream)
+    _check(ctx, s, "mge_kmeans")
+    return a, cen, iters.value
 
 
 def mge_graph_info(g):

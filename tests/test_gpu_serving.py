@@ -109,3 +109,39 @@ def test_eight_slots_every_request_matches_alone(gpu_lib, monkeypatch):
             assert np.allclose(lam, lam0, rtol=1e-10, atol=0)
             assert np.max(np.abs(V - V0)) < 1e-8
             assert mge.mge_release(ctx.h, t) == 0
+
+
+def test_requests_given_as_points(gpu_lib):
+    """A request given as points runs kNN graph, operators and embedding on the device; its
+    result equals the graph built by mge_knn_graph and embedded alone."""
+    mge = gpu_lib
+    sets = [(mg.sample_points("sphere", 4000, 31), 10, 8, "fp32"),
+            (mg.sample_points("square", 3000, 32), 8, 4, "fp32"),
+            (mg.sample_points("swiss_roll", 6000, 33), 10, 8, "bf16")]
+    with mge.Context(0) as ctx:
+        alone = []
+        for P, k, K, p in sets:
+            g = mge.mge_knn_graph(ctx.h, P, k)
+            rp, col, w = mge.mge_graph_csr(g)
+            n, _, _ = mge.mge_graph_info(g)
+            h, s = mge.mge_build_graph_ops(ctx.h, n, rp, col, w, True, mge.ops_opts(p))
+            mge.mge_graph_destroy(g)
+            lam, V, info, s2 = mge.mge_embed(ctx.h, h, K, 1e-5, mge.embed_opts(p, guard=4))
+            mge.mge_ops_destroy(h)
+            alone.append((lam, V.T))
+    with mge.Context(0) as ctx:
+        tickets = []
+        for P, k, K, p in sets:
+            r = mge.mge_request()
+            r.n, r.K, r.tol, r.precision, r.guard = P.shape[0], K, 1e-5, mge.PRECISION[p], 4
+            Pc = np.ascontiguousarray(P)
+            r.points, r.dim, r.knn = Pc.ctypes.data, P.shape[1], k
+            tickets.append(mge.mge_submit(ctx.h, r))
+        for (P, k, K, p), t, (lam0, V0) in zip(sets, tickets, alone):
+            s, r = mge.mge_poll(ctx.h, t, -1)
+            assert s == 0 and r.status == 0, (s, r.status)
+            lam = np.ctypeslib.as_array(r.lambda_, shape=(K,)).copy()
+            V = np.ctypeslib.as_array(r.V, shape=(K, P.shape[0])).T.copy()
+            assert np.allclose(lam, lam0, rtol=1e-10, atol=0)
+            assert np.max(np.abs(V - V0)) < 1e-8
+            mge.mge_release(ctx.h, t)
