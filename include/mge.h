@@ -354,6 +354,21 @@ mge_status mge_embed_batch(mge_ctx* ctx, int count, const mge_ops* const* ops, c
                            double tol, const mge_embed_opts* opts, double* const* lambda,
                            void* const* V, mge_embed_info* info);
 
+/* ---- betweenness centrality and VBC (Sec. 3.3) ------------------------------------- */
+
+/* The paper qualifies an input graph as a manifold graph by the variance of its nodes'
+ * betweenness centralities (VBC, Sec. 3.3, Table 1):
+ *   C_B(i) = sum over ordered pairs (s, t), s != t, both != i, of sigma_st(i) / sigma_st,
+ * sigma_st the number of shortest paths from s to t (counted in hops; the graph's weights are
+ * similarities, not lengths) and sigma_st(i) those through i; pairs without a path add
+ * nothing.  VBC = (1/n) sum_i (C_B(i) - mean C_B)^2.
+ * row_ptr [n+1], col: CSR of an undirected graph (both directions stored), host or device per
+ * on_device; cb [n] FP64 written (host or device per on_device); vbc (host, may be NULL).
+ * Cost O(n nnz): meant for the graph sizes the paper qualifies (hundreds to tens of
+ * thousands of nodes).  Errors: MGE_EINVAL (malformed CSR), MGE_ENOMEM, MGE_EDEVICE. */
+mge_status mge_betweenness(mge_ctx* ctx, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                           int on_device, double* cb, double* vbc, void* stream);
+
 /* ---- k-means of the embedding (Sec. 5.2) ------------------------------------------- */
 
 /* The paper clusters its embeddings with kmeans (Sec. 5.2, Table 3).  Lloyd's algorithm in

@@ -543,6 +543,42 @@ mge_status mge_graph_destroy(mge_graph* g) {
   return MGE_OK;
 }
 
+// ---- betweenness centrality and VBC ----------------------------------------------------------
+
+mge_status mge_betweenness(mge_ctx* c, int64_t n, const int64_t* row_ptr, const int32_t* col, int on_device,
+                           double* cb, double* vbc, void* stream) {
+  if (!c || !row_ptr || !cb || n < 1) return MGE_EINVAL;
+  Ctx* ctx = &c->impl;
+  if (ctx->closed) return MGE_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return MGE_EDEVICE;
+  cudaStream_t st = pick_stream(ctx, stream);
+  DevBuf<int64_t> rpd;
+  DevBuf<int32_t> cold;
+  DevBuf<double> cbd;
+  const int64_t* rp = row_ptr;
+  const int32_t* cl = col;
+  double* out = cb;
+  if (on_device) {
+    MGE_TRY(check_block_ptr(ctx, row_ptr, "betweenness", "row_ptr"));
+    MGE_TRY(check_block_ptr(ctx, cb, "betweenness", "cb"));
+  } else {
+    const int64_t nnz = row_ptr[n];
+    if (row_ptr[0] != 0 || nnz < 0 || (nnz > 0 && !col)) { set_error(ctx, "betweenness: malformed CSR"); return MGE_EINVAL; }
+    MGE_TRY(rpd.scratch(ctx, (size_t)n + 1, st));
+    MGE_TRY(cold.scratch(ctx, (size_t)std::max<int64_t>(nnz, 1), st));
+    MGE_TRY(cbd.scratch(ctx, (size_t)n, st));
+    MGE_CUDA(ctx, cudaMemcpyAsync(rpd.p, row_ptr, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (nnz > 0) MGE_CUDA(ctx, cudaMemcpyAsync(cold.p, col, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    rp = rpd.p; cl = cold.p; out = cbd.p;
+  }
+  MGE_TRY(betweenness_run(ctx, st, n, rp, cl, out, vbc));
+  if (!on_device) {
+    MGE_CUDA(ctx, cudaMemcpyAsync(cb, cbd.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  }
+  return MGE_OK;
+}
+
 // ---- k-means of the embedding --------------------------------------------------------------
 
 mge_status mge_kmeans(mge_ctx* c, int64_t n, int K, const double* X, int C, const double* centres0, int max_iters,

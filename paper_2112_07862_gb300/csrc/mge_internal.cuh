@@ -236,6 +236,11 @@ mge_status knn_graph_build(Ctx* ctx, cudaStream_t st, int64_t n, int dim, const 
 mge_status kmeans_run(Ctx* ctx, cudaStream_t st, int64_t n, int K, const double* X, int C, double* centres,
                       int max_iters, int32_t* assign, int* iters_out);
 
+// Betweenness centrality cb [n] (device) of the CSR graph (device) and, vbc_out not NULL,
+// its population variance; betweenness.cu.
+mge_status betweenness_run(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* rp, const int32_t* col, double* cb,
+                           double* vbc_out);
+
 // ---------------------------------------------------------------------------------------
 // LOBPCG operator description handed to the solver
 // ---------------------------------------------------------------------------------------

@@ -26,7 +26,7 @@ EXPORTS = [
     "mge_create", "mge_destroy", "mge_strerror", "mge_ctx_last_error", "mge_ctx_stats",
     "mge_ctx_set_timing", "mge_ctx_reset_stats", "mge_build_graph_ops", "mge_build_graph_ops_batch", "mge_ops_destroy",
     "mge_ops_info", "mge_ops_export", "mge_ops_node_order", "mge_ops_apply", "mge_ops_apply_inplace", "mge_embed", "mge_embed_batch", "mge_submit", "mge_poll",
-    "mge_release", "mge_kmeans", "mge_knn_graph", "mge_graph_info", "mge_graph_csr", "mge_graph_export", "mge_graph_destroy",
+    "mge_release", "mge_betweenness", "mge_kmeans", "mge_knn_graph", "mge_graph_info", "mge_graph_csr", "mge_graph_export", "mge_graph_destroy",
 ]
 
 
@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH):
         "mge_release": (i, [vp, u64]),
         "mge_knn_graph": (i, [vp, i64, i, vp, i, i, vp, C.POINTER(vp)]),
         "mge_kmeans": (i, [vp, i64, i, vp, i, vp, i, i, vp, vp, C.POINTER(i), vp]),
+        "mge_betweenness": (i, [vp, i64, vp, vp, i, vp, C.POINTER(d), vp]),
         "mge_graph_info": (i, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(d)]),
         "mge_graph_csr": (i, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
         "mge_graph_export": (i, [vp, vp, vp, vp, i]),
@@ -206,6 +207,23 @@ def mge_knn_graph(ctx, points, k: int, stream=None):
     s = load().mge_knn_graph(ctx, n, dim, _ptr(points), 1 if on_device else 0, int(k), stream, C.byref(h))
     _check(ctx, s, "mge_knn_graph")
     return h
+
+
+def mge_betweenness(ctx, n, row_ptr, col, stream=None):
+    """Betweenness centralities (numpy [n] on the host path, a torch tensor when row_ptr and
+    col are torch CUDA tensors) and the VBC."""
+    vbc = C.c_double()
+    if hasattr(row_ptr, "data_ptr"):
+        import torch
+        cb = torch.empty(int(n), dtype=torch.float64, device=row_ptr.device)
+        s = load().mge_betweenness(ctx, int(n), _ptr(row_ptr), _ptr(col), 1, _ptr(cb), C.byref(vbc), stream)
+    else:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        cl = np.ascontiguousarray(col, dtype=np.int32)
+        cb = np.empty(int(n), np.float64)
+        s = load().mge_betweenness(ctx, int(n), _ptr(rp), _ptr(cl), 0, _ptr(cb), C.byref(vbc), stream)
+    _check(ctx, s, "mge_betweenness")
+    return cb, vbc.value
 
 
 def mge_kmeans(ctx, X, centres0, max_iters: int, stream=None):
