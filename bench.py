@@ -55,7 +55,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--serve-requests", type=int, default=32)
     p.add_argument("--no-serving", action="store_true")
-    p.add_argument("--batch-graphs", type=int, default=64)
+    p.add_argument("--batch-graphs", type=int, default=512)
+    p.add_argument("--no-extras", action="store_true", help="skip the kNN, k-means and betweenness lines")
     p.add_argument("--no-batch", action="store_true")
     return p.parse_args()
 
@@ -325,10 +326,11 @@ def run_ours(a, dist):
 # ---------------------------------------------------------------------------------------
 def run_batch(a):
     """Graphs with N log-uniform in [2,000, 50,000], shape square / torus / swiss roll, k in
-    {8, 10, 12}, K in {4, 8} (seed 4 + index), FP32 blocks, tol 1e-5.  The operators are
-    built by mge_build_graph_ops_batch (concurrent builds on 8 host threads and streams;
-    timed against one mge_build_graph_ops after another); then every embedding runs as a
-    branch of ONE CUDA graph launch, and, for comparison, one mge_embed after another.
+    {8, 10, 12}, K in {4, 8} (seed 4 + index), FP32 blocks, tol 1e-5.  The points are sampled
+    on the host; their kNN graphs are built on the device (mge_knn_graph), the operators by
+    mge_build_graph_ops_batch (concurrent builds on 8 host threads and streams; timed against
+    one mge_build_graph_ops after another); then every embedding runs as a branch of ONE CUDA
+    graph launch and, for comparison, one mge_embed after another.
     Embedding throughput = sum of N / device time of the launch(es)."""
     import numpy as np
     import torch
@@ -338,26 +340,34 @@ def run_batch(a):
 
     rng = np.random.default_rng(4)
     shapes = ["square", "torus", "swiss_roll"]
-    graphs = []
+    specs = []
     for i in range(a.batch_graphs):
         n = int(round(float(np.exp(rng.uniform(np.log(2_000), np.log(50_000))))))
         shape = shapes[int(rng.integers(3))]
         k = int(rng.choice([8, 10, 12]))
         K = int(rng.choice([4, 8]))
-        graphs.append((mg.manifold_graph(shape, n, k, 4 + i), K))
-    nodes = sum(g.n for g, _ in graphs)
-    Ks = [K for _, K in graphs]
+        specs.append((mg.sample_points(shape, n, 4 + i), k, K))
+    nodes = sum(P.shape[0] for P, _, _ in specs)
+    Ks = [K for _, _, K in specs]
     with mge.Context(0) as ctx:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for g, _ in graphs:
-            mge.mge_ops_destroy(mge.mge_build_graph_ops(ctx.h, g.n, g.row_ptr, g.col, g.w, False,
-                                                        mge.ops_opts("fp32"))[0])
+        graphs = [mge.mge_knn_graph(ctx.h, P, k) for P, k, _ in specs]
+        t_knn = time.perf_counter() - t0
+        csr = []
+        for g in graphs:
+            n, _, _ = mge.mge_graph_info(g)
+            rp, col, w = mge.mge_graph_csr(g)
+            csr.append((n, rp, col, w))
+        t0 = time.perf_counter()
+        for n, rp, col, w in csr:
+            mge.mge_ops_destroy(mge.mge_build_graph_ops(ctx.h, n, rp, col, w, True, mge.ops_opts("fp32"))[0])
         t_build_seq = time.perf_counter() - t0
         t0 = time.perf_counter()
-        ops, _, _ = mge.mge_build_graph_ops_batch(ctx.h, [(g.n, g.row_ptr, g.col, g.w) for g, _ in graphs],
-                                                  False, mge.ops_opts("fp32"))
+        ops, _, _ = mge.mge_build_graph_ops_batch(ctx.h, csr, True, mge.ops_opts("fp32"))
         t_build = time.perf_counter() - t0
+        for g in graphs:
+            mge.mge_graph_destroy(g)
         eo = mge.embed_opts("fp32")
         mge.mge_embed_batch(ctx.h, ops, Ks, a.tol, eo)            # warm-up (allocations, instantiation)
         t0 = time.perf_counter()
@@ -372,20 +382,21 @@ def run_batch(a):
         for o in ops:
             mge.mge_ops_destroy(o)
     iters = [i.iters for i in infos]
-    return {"graphs": len(graphs), "nodes": int(nodes), "status": int(s),
+    return {"graphs": len(specs), "nodes": int(nodes), "status": int(s),
             "converged": int(sum(1 for i in infos if i.status == 0)),
             "value": nodes / (dev_batch / 1e3), "unit": UNIT,
             "batch_launch_ms": dev_batch, "batch_call_ms": 1e3 * t_batch,
             "one_by_one_device_ms": dev_seq, "one_by_one_call_ms": 1e3 * t_seq,
             "one_by_one_value": nodes / (dev_seq / 1e3),
+            "knn_ms": 1e3 * t_knn,
             "build_ms_batch": 1e3 * t_build, "build_ms_one_by_one": 1e3 * t_build_seq,
-            "with_build_value": nodes / (t_build + t_batch),
+            "with_build_value": nodes / (t_knn + t_build + t_batch),
             "iters_min_max": [min(iters), max(iters)],
-            "workload": f"{len(graphs)} graphs, N log-uniform in [2000, 50000] (seed 4 + index), square/torus/"
-                        "swiss roll, k in {8,10,12}, K in {4,8}, FP32 blocks, tol 1e-5; value = sum N / device "
-                        "time of the one batch launch (embedding only); with_build_value = sum N / (wall time of "
-                        "mge_build_graph_ops_batch, 8 host threads and streams, + wall time of the batch "
-                        "embedding call), host CSR in, host V out"}
+            "workload": f"{len(specs)} graphs, N log-uniform in [2000, 50000] (seed 4 + index), square/torus/"
+                        "swiss roll, k in {8,10,12}, K in {4,8}, FP32 blocks, relative residual 1e-5; value = "
+                        "sum N / device time of the one batch launch (embedding only); with_build_value = sum N / "
+                        "(wall time of the kNN graphs on the device + mge_build_graph_ops_batch (8 host threads "
+                        "and streams) + the batch embedding call), host points in, host V out"}
 
 
 # ---------------------------------------------------------------------------------------
@@ -394,9 +405,10 @@ def run_batch(a):
 def run_serving(a):
     """Requests of uneven size arrive as a Poisson stream (200 req/s, seed 5): N log-uniform
     in [1,000, 500,000], shape square / sphere / swiss roll, 10-NN, K in {2, 4, 8, 16},
-    FP32 blocks, tolerance 1e-5.  The graphs are built before the clock starts; each request
-    is submitted at its arrival time and the library's slots admit and run the requests
-    concurrently on the device.  Latency is the library's submit-to-completion time."""
+    FP32 or BF16 (seeded choice), relative residual 1e-5.  Each request carries its points:
+    the library builds the kNN graph, the operators and the embedding on the device.  Requests
+    are submitted at their arrival times and the library's slots admit and run them
+    concurrently.  Latency is the library's submit-to-completion time."""
     import numpy as np
 
     import manifold_graphs as mg
@@ -409,28 +421,29 @@ def run_serving(a):
         n = int(round(float(np.exp(rng.uniform(np.log(1_000), np.log(500_000))))))
         shape = shapes[int(rng.integers(3))]
         K = int(rng.choice([2, 4, 8, 16]))
-        reqs.append((mg.manifold_graph(shape, n, 10, 500 + i), K))
+        prec = mge.MGE_BF16 if rng.random() < 0.5 else mge.MGE_FP32
+        reqs.append((np.ascontiguousarray(mg.sample_points(shape, n, 500 + i)), K, prec))
     arrivals = np.cumsum(rng.exponential(1.0 / 200.0, len(reqs)))
 
-    def request(g, K):
+    def request(P, K, prec):
         r = mge.mge_request()
-        r.n, r.row_ptr, r.col, r.w = g.n, g.row_ptr.ctypes.data, g.col.ctypes.data, g.w.ctypes.data
-        r.K, r.tol, r.precision, r.guard, r.maxiter, r.seed = K, 1e-5, mge.MGE_FP32, 0, 0, 0
+        r.n, r.points, r.dim, r.knn = P.shape[0], P.ctypes.data, P.shape[1], 10
+        r.K, r.tol, r.precision, r.guard, r.maxiter, r.seed = K, a.tol, prec, 0, 0, 0
         return r
 
     with mge.Context(0) as ctx:
         # one small request first, so that the slots and their streams exist
-        g0 = mg.manifold_graph("square", 1_000, 10, 499)
-        t = mge.mge_submit(ctx.h, request(g0, 2))
+        P0 = np.ascontiguousarray(mg.sample_points("square", 1_000, 499))
+        t = mge.mge_submit(ctx.h, request(P0, 2, mge.MGE_FP32))
         mge.mge_poll(ctx.h, t, -1)
         mge.mge_release(ctx.h, t)
         tickets = []
         t0 = time.perf_counter()
-        for (g, K), ta in zip(reqs, arrivals):
+        for (P, K, prec), ta in zip(reqs, arrivals):
             dt = t0 + ta - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
-            tickets.append(mge.mge_submit(ctx.h, request(g, K)))
+            tickets.append(mge.mge_submit(ctx.h, request(P, K, prec)))
         lat, queue, ok, statuses = [], [], 0, {}
         for t in tickets:
             s, r = mge.mge_poll(ctx.h, t, -1)
@@ -442,16 +455,102 @@ def run_serving(a):
             queue.append(r.queue_ms)
             mge.mge_release(ctx.h, t)
         wall = time.perf_counter() - t0
-    nodes = sum(g.n for g, _ in reqs)
-    return {"requests": len(reqs), "converged": ok, "statuses": statuses, "offered_req_per_s": 200.0,
+    nodes = sum(P.shape[0] for P, _, _ in reqs)
+    return {"requests": len(reqs), "bf16_requests": int(sum(1 for _, _, p in reqs if p == mge.MGE_BF16)), "converged": ok, "statuses": statuses, "offered_req_per_s": 200.0,
             "served_req_per_s": len(reqs) / wall, "value": nodes / wall, "unit": UNIT,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "queue_p50_ms": float(np.percentile(queue, 50)), "queue_p99_ms": float(np.percentile(queue, 99)),
             "nodes": int(nodes), "wall_s": wall,
             "workload": "Poisson 200 req/s (seed 5), N log-uniform in [1000, 500000], square/sphere/swiss "
-                        "roll, 10-NN, K in {2,4,8,16}, FP32 blocks, tol 1e-5; graphs built before the clock; "
-                        "latency = submit to completion (host clock), host CSR in, host V out",
+                        "roll, 10-NN, K in {2,4,8,16}, FP32 or BF16 (seeded), relative residual 1e-5; each request "
+                        "carries its points (kNN graph, operators and embedding on the device); latency = submit "
+                        "to completion (host clock), host points in, host V out",
             "slots": int(os.environ.get("MGE_SERVE_SLOTS", "4"))}
+
+
+# ---------------------------------------------------------------------------------------
+# the steps around the path: kNN graph from points, k-means of the embedding, VBC
+# ---------------------------------------------------------------------------------------
+def _event_ms(fn, reps=3):
+    """Best device time of fn() over reps calls (CUDA events on torch's current stream, which
+    fn's library calls are handed), after one untimed call."""
+    import torch
+    fn()
+    best = None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    return best
+
+
+def run_extras(a):
+    import numpy as np
+    import torch
+
+    import manifold_graphs as mg
+    from paper_2112_07862_gb300 import mge
+
+    out = {}
+    sptr = torch.cuda.current_stream().cuda_stream
+    with mge.Context(0) as ctx:
+        # kNN graph of the workload's points (device points in, device CSR out)
+        P = mg.sample_points(a.shape, a.n, a.seed)
+        Pd = torch.from_numpy(np.ascontiguousarray(P)).cuda()
+        torch.cuda.synchronize()
+        holder = {}
+
+        def knn():
+            if "g" in holder:
+                mge.mge_graph_destroy(holder.pop("g"))
+            holder["g"] = mge.mge_knn_graph(ctx.h, Pd, a.knn, stream=sptr)
+        ms = _event_ms(knn)
+        n, nnz, sigma = mge.mge_graph_info(holder["g"])
+        out["knn"] = {"workload": f"{a.shape} N={a.n} points (dim {P.shape[1]}), exact {a.knn}-NN, union, "
+                                  "Gaussian weights; device points in, device CSR out",
+                      "ms": ms, "value": a.n / (ms / 1e3), "unit": "points/s", "nnz": int(nnz),
+                      "launches_per_call": "13 kernels (bbox, 2 binning passes, scan, scatter, query, sigma, "
+                                           "symmetrisation, weights)"}
+        # k-means (C = 16, at most 50 steps) of that graph's embedding
+        rp, col, w = mge.mge_graph_csr(holder["g"])
+        h, s = mge.mge_build_graph_ops(ctx.h, n, rp, col, w, True, mge.ops_opts(a.precision, stream=sptr))
+        Vd = torch.empty((a.K, n), dtype=torch.float64, device="cuda")
+        mge.mge_embed(ctx.h, h, a.K, a.tol, mge.embed_opts(a.precision, v_on_device=True, stream=sptr), Vd)
+        mge.mge_ops_destroy(h)
+        mge.mge_graph_destroy(holder.pop("g"))
+        C = 16
+        idx = torch.from_numpy(np.random.default_rng(6).choice(n, C, replace=False)).cuda()
+        C0 = Vd[:, idx].T.contiguous()
+        torch.cuda.synchronize()
+        steps = {}
+
+        def km():
+            steps["s"] = mge.mge_kmeans(ctx.h, Vd, C0, 50, stream=sptr)[2]
+        ms = _event_ms(km)
+        out["kmeans"] = {"workload": f"the {a.K}-dimensional embedding of that graph (N={n}), {C} clusters from "
+                                     "seeded initial rows, Lloyd, at most 50 steps",
+                         "ms": ms, "steps": steps["s"], "value": n * steps["s"] / (ms / 1e3),
+                         "unit": "point-steps/s"}
+        # betweenness centrality and VBC of a 5,000-node manifold graph
+        g = mg.manifold_graph(a.shape, 5000, a.knn, a.seed)
+        rpd = torch.from_numpy(g.row_ptr).cuda()
+        cold = torch.from_numpy(g.col).cuda()
+        torch.cuda.synchronize()
+        res = {}
+
+        def bc():
+            res["v"] = mge.mge_betweenness(ctx.h, g.n, rpd, cold, stream=sptr)[1]
+        ms = _event_ms(bc, reps=2)
+        out["betweenness"] = {"workload": f"{a.shape} N=5000 {a.knn}-NN graph (nnz {g.nnz}): C_B of every node "
+                                          "(all n sources, Brandes) and VBC",
+                              "ms": ms, "vbc": res["v"], "value": g.n * g.nnz / (ms / 1e3),
+                              "unit": "edge traversals/s (n nnz per call)"}
+    return out
 
 
 # ---------------------------------------------------------------------------------------
@@ -524,6 +623,8 @@ def main():
             res["batch"] = run_batch(a)
         if dist.world == 1 and not a.no_serving:
             res["serving"] = run_serving(a)
+        if dist.world == 1 and not a.no_extras:
+            res.update(run_extras(a))
         print(json.dumps(res), flush=True)
     dist.close()
 
