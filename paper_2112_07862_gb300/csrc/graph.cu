@@ -847,7 +847,7 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
       qop.dinv = (o.precision == MGE_FP64) ? (const void*)ops->dinv_q.p : (const void*)ops->dinv_q32.p;
       qop.norm = ops->norm_q; qop.bmax = 1.0; qop.deflate = true; qop.beta = ops->beta_q;
       qop.precond_degree = o.eps_precond_degree > 0 ? std::min(o.eps_precond_degree, 64) : kDefaultEpsPrecondDegree;
-      qop.rr_fp64 = true;     // Rayleigh-Ritz in FP64: the relative residual eps needs (see mge_embed)
+      qop.rr_fp64 = o.precision == MGE_FP64;
       qop.pc_bf16 = o.precision == MGE_BF16;
       if (qop.pc_bf16) qop.precond_degree = std::min(qop.precond_degree, kBf16MaxPrecondDegree);
       if (ops->q_sl.built()) {
