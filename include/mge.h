@@ -295,7 +295,7 @@ typedef struct {
                                  d = 1 is the Jacobi preconditioner; each degree above 1
                                  costs one SpMM of L' per iteration and cuts the iteration
                                  count about in proportion.  The paper leaves the
-                                 preconditioner open.  0 = default 48; at most 64.          */
+                                 preconditioner open.  0 = default 64; at most 64.          */
   int         rr_fp64;        /* arithmetic of the Rayleigh-Ritz eigensolve and of the
                                  Cholesky that B-normalises W, for FP32 blocks: 0 (default)
                                  the inverse-pencil FP32 solve described under MGE_FP32;

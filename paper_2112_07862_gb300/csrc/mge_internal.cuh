@@ -245,9 +245,10 @@ mge_status betweenness_run(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* 
 // LOBPCG operator description handed to the solver
 // ---------------------------------------------------------------------------------------
 // default degrees of the Chebyshev preconditioner of the LOBPCG solves (measured on a
-// 200k-node swiss roll: total solve time is flat within about 5% from 40 to 64 for the
-// embedding and from 24 to 32 for the eps solve)
-constexpr int kDefaultPrecondDegree = 48;
+// 200k-node swiss roll, K = 8, m = 16, relative residual 1e-5: embedding 145 / 73 / 44 / 27 /
+// 21 iterations and 162 / 95 / 65 / 49 / 45 ms at degree 16 / 24 / 32 / 48 / 64; the eps
+// solve converges in about 23 iterations at 24)
+constexpr int kDefaultPrecondDegree = 64;
 constexpr int kDefaultEpsPrecondDegree = 24;
 // BF16 preconditioner blocks: the Chebyshev polynomial amplifies the bottom of the spectrum by
 // about 2 d^2 against the top, so BF16 rounding (u = 2^-8) of its iterates leaves the

@@ -4,7 +4,9 @@
                          weights: eps = lambda_2(Q) (Sec. 4.2), mu (Eq. 9), ||A||_G,
                          max b_i, and the first K + 2 = 10 generalized eigenvalues of
                          (A, B) (Eq. 10-11), all in FP64.
-  oracle/_cache/<key>.npz   the matching eigenvectors (n x 10 FP64, 16 MB: too large to
+  sphere_2m.json         2,000,000 points uniform on the unit sphere (seed 3), 10-NN: the
+                         same quantities, first K + 2 = 18 eigenvalues.
+  oracle/_cache/<key>.npz   the matching eigenvectors (n x 10 or n x 18 FP64: too large to
                          commit, so cached under a git-ignored folder keyed by the
                          workload and recomputed when missing).
 
@@ -37,6 +39,7 @@ CACHE = os.path.join(ROOT, "oracle", "_cache")
 # name -> (shape, n, k, seed, number of eigenpairs kept)
 WORKLOADS = {
     "swiss_roll_200k": ("swiss_roll", 200_000, 10, 2, 10),
+    "sphere_2m": ("sphere", 2_000_000, 10, 3, 18),
 }
 
 
