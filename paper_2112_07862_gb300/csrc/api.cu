@@ -759,6 +759,7 @@ mge_status mge_embed(mge_ctx* c, const mge_ops* o, int K, double tol, const mge_
   l.precond_degree = e.precond_degree > 0 ? std::min(e.precond_degree, 64) : kDefaultPrecondDegree;
   if (bf16) l.precond_degree = std::min(l.precond_degree, kBf16MaxPrecondDegree);
   l.rr_fp64 = rr_fp64_for(e, prec);
+  l.gram_cuda_cores = e.gram_cuda_cores != 0;
   mge_status s = lobpcg_solve(ctx, st, l, prec, K, m, tol, e.maxiter, e.seed, e.check_every, e.use_graph != 0,
                               x0, x0c, vout, &r);
   if (s != MGE_OK && s != MGE_ENOTCONVERGED) {
@@ -816,6 +817,7 @@ mge_status mge_embed_batch(mge_ctx* c, int count, const mge_ops* const* ops, con
     if (bf16) lops[i].precond_degree = std::min(lops[i].precond_degree, kBf16MaxPrecondDegree);
     lops[i].rr_fp64 = rr_fp64_for(e, prec);
     lops[i].pc_bf16 = bf16;
+    lops[i].gram_cuda_cores = e.gram_cuda_cores != 0;
   }
   cudaStream_t st = pick_stream(ctx, e.stream);
   // V buffers: the caller's device arrays, or scratch copied to the caller's host arrays

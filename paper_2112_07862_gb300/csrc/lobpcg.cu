@@ -1160,7 +1160,7 @@ struct Solver {
 
   void launch_rr_(int nb, int nx) {
     RRArgs r{};
-    r.sm = sm; r.smt = smt; r.is_double = sizeof(T) == 8; r.ncl = 1;
+    r.sm = sm; r.smt = smt; r.is_double = sizeof(T) == 8; r.ncl = gram_ncl;
     r.M = M; r.nb = nb; r.nx = nx; r.tau = tau; r.tau_p = tau_p; r.st = state;
     launch_rr(st, r, inverse_rr);
     MGE_LAUNCHED(ctx, 1);
@@ -1317,18 +1317,43 @@ struct Solver {
                 MAXS * MAXM, op.deflate);
   }
 
-  void launch_gram_s(int nb) {
+  // S-side Grams on the tensor cores (gram_tc.cu) for FP32 blocks of width 12, 16, 24 with the
+  // full basis [X W P]
+  static constexpr bool kTcWidth = sizeof(T) == 4 && (M == 12 || M == 16 || M == 24);
+  int gram_ncl = 1;
+  bool use_tc_gram() const { return kTcWidth && !op.gram_cuda_cores; }
+
+  mge_status launch_gram_s_tc() {
+    if constexpr (kTcWidth) {
+      GramTcArgs g{};
+      g.n = n;
+      g.S[0] = X.p; g.S[1] = W.p; g.S[2] = P.p;
+      g.AS[0] = AX.p; g.AS[1] = AW.p; g.AS[2] = AP.p;
+      g.b = static_cast<const float*>(op.b);
+      g.outA = &sm->partA[0][0];
+      g.outB = &sm->partB[0][0];
+      g.st = state;
+      MGE_CUDA(ctx, gram_tc_launch<M>(ctx, st, g, gram_tc_clusters<M>(ctx, n)));
+      MGE_LAUNCHED(ctx, 1);
+    }
+    return MGE_OK;
+  }
+
+  mge_status launch_gram_s(int nb) {
+    gram_ncl = 1;
+    if (nb == 3 && use_tc_gram()) return launch_gram_s_tc();
     const T* L[3] = {X.p, W.p, P.p};
     const T* R[3] = {AX.p, AW.p, AP.p};
     if (nb == 1) { L[0] = W.p; R[0] = AW.p; }
     launch_gram(nb, L, nb, R, nb, L, true, op.b != nullptr, &sm->partA[0][0], &sm->partB[0][0], MAXS,
                 MAXS * MAXS, false);
+    return MGE_OK;
   }
 
   mge_status iteration(int nb, bool timed) {
     bool hp = nb == 3;
     MGE_TRY(launch_spmm(true, hp, timed));
-    launch_gram_s(nb);
+    MGE_TRY(launch_gram_s(nb));
     launch_rr_(nb, M);
     launch_update(nb, false, true);
     MGE_TRY(launch_cheb(timed));
@@ -1346,14 +1371,14 @@ struct Solver {
     launch_gram_w(false, false);
     launch_wprep_(false, false, false);
     MGE_TRY(launch_spmm(false, false, timed));
-    launch_gram_s(1);
+    MGE_TRY(launch_gram_s(1));
     launch_rr_(1, 0);
     launch_update(1, true, false);
     MGE_TRY(launch_cheb(timed));
     launch_gram_w(true, false);
     launch_wprep_(true, false, true);
     MGE_TRY(launch_spmm(true, false, timed));
-    launch_gram_s(2);
+    MGE_TRY(launch_gram_s(2));
     launch_rr_(2, M);
     launch_update(2, false, true);
     MGE_TRY(launch_cheb(timed));
@@ -1576,6 +1601,9 @@ mge_status prepare_solver(Solver<T, M>& s) {
   MGE_CUDA(ctx, cudaFuncSetAttribute(k_gram<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
   MGE_CUDA(ctx, (spmm_configure<T, M>()));
   MGE_CUDA(ctx, (cheb_configure<T, T, T, M>()));
+  if constexpr (Solver<T, M>::kTcWidth) {
+    if (s.use_tc_gram()) MGE_CUDA(ctx, gram_tc_configure<M>());
+  }
   if constexpr (sizeof(T) == 4) {
     if (s.pc_bf16) {
       MGE_CUDA(ctx, (cheb_configure<float, __nv_bfloat16, __nv_bfloat16, M>()));

@@ -266,6 +266,24 @@ struct ChebArgs {
   State* st;
 };
 
+// Tensor-core Grams of S = [X W P] (gram_tc.cu): G_A = S^T [AX AW AP] into outA and
+// G_B = S^T B S into outB, added with FP64 atomics (the accumulators start at zero).
+struct GramTcArgs {
+  int64_t n;
+  const float* S[3];
+  const float* AS[3];
+  const float* b;            // NULL: B = I (else padded with 4 zeros)
+  double* outA;
+  double* outB;
+  State* st;
+};
+template <int M>
+cudaError_t gram_tc_configure();
+template <int M>
+int gram_tc_clusters(const Ctx* ctx, int64_t n);
+template <int M>
+cudaError_t gram_tc_launch(const Ctx* ctx, cudaStream_t st, const GramTcArgs& a, int clusters);
+
 // Launches the step on stream st; max_tile_slots (the densest tile of the sliced copy) sizes
 // the shared-memory stages.  S is the storage type of x, R, d and d_out, SO that of x_out
 // (T, or __nv_bfloat16 with T = float).  cheb_configure raises the dynamic shared-memory limit.

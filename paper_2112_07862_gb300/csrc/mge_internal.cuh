@@ -271,6 +271,7 @@ struct LobOp {
   int precond_degree = 1;          // Chebyshev preconditioner degree (1: Jacobi)
   bool rr_fp64 = false;            // FP32 blocks: Rayleigh-Ritz and W's Cholesky in FP64
   bool pc_bf16 = false;            // FP32 blocks: the preconditioner's blocks in BF16
+  bool gram_cuda_cores = false;    // FP32 blocks: Rayleigh-Ritz Grams on the CUDA cores only
   // operator the preconditioner applies, in the same difference form (pc_ptr NULL: the
   // operator itself); its diagonal scaling and Gershgorin bound
   const int64_t* pc_ptr = nullptr;

@@ -53,7 +53,8 @@ class mge_embed_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("guard", C.c_int), ("maxiter", C.c_int), ("seed", C.c_uint64),
                 ("check_every", C.c_int), ("use_graph", C.c_int), ("x0", C.c_void_p), ("x0_cols", C.c_int),
                 ("x0_on_device", C.c_int), ("v_on_device", C.c_int), ("stream", C.c_void_p),
-                ("precond_degree", C.c_int), ("rr_fp64", C.c_int)]
+                ("precond_degree", C.c_int), ("rr_fp64", C.c_int),
+                ("gram_cuda_cores", C.c_int)]
 
 
 class mge_embed_info(C.Structure):
@@ -451,7 +452,8 @@ def ops_opts(precision="fp32", eps=None, mu=None, eps_tol=0.0, seed=0, stream=No
 
 
 def embed_opts(precision="fp32", guard=0, maxiter=0, seed=0, check_every=0, use_graph=True, x0=None,
-               v_on_device=False, stream=None, precond_degree=0, rr_fp64=False) -> mge_embed_opts:
+               v_on_device=False, stream=None, precond_degree=0, rr_fp64=False,
+               gram_cuda_cores=False) -> mge_embed_opts:
     o = mge_embed_opts()
     o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     o.guard = guard
@@ -467,6 +469,7 @@ def embed_opts(precision="fp32", guard=0, maxiter=0, seed=0, check_every=0, use_
     o.stream = stream
     o.precond_degree = precond_degree
     o.rr_fp64 = 1 if rr_fp64 else 0
+    o.gram_cuda_cores = 1 if gram_cuda_cores else 0
     return o
 
 
