@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--batch-graphs", type=int, default=512)
     p.add_argument("--no-extras", action="store_true", help="skip the kNN, k-means and betweenness lines")
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--batch-workers", type=int, default=8, help="host threads of mge_build_graph_ops_batch")
     return p.parse_args()
 
 
@@ -364,7 +365,7 @@ def run_batch(a):
             mge.mge_ops_destroy(mge.mge_build_graph_ops(ctx.h, n, rp, col, w, True, mge.ops_opts("fp32"))[0])
         t_build_seq = time.perf_counter() - t0
         t0 = time.perf_counter()
-        ops, _, _ = mge.mge_build_graph_ops_batch(ctx.h, csr, True, mge.ops_opts("fp32"))
+        ops, _, _ = mge.mge_build_graph_ops_batch(ctx.h, csr, True, mge.ops_opts("fp32"), workers=a.batch_workers)
         t_build = time.perf_counter() - t0
         for g in graphs:
             mge.mge_graph_destroy(g)

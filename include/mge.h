@@ -304,11 +304,12 @@ typedef struct {
                                  iterations, 1.8 ms each; FP64 36 iterations, 3.6 ms each;
                                  eigenvalues within 1e-6 of the oracle either way.  FP64
                                  blocks always use FP64.                                    */
-  int         gram_cuda_cores; /* FP32 blocks of width 12, 16 or 24: 0 (default) computes the
-                                 Rayleigh-Ritz Grams [X W P]^T A [X W P] and [X W P]^T B [X W P]
-                                 on the tensor cores (tcgen05, TF32 with each value split in
-                                 two so that products keep about 2^-21 relative accuracy); 1
-                                 computes them on the CUDA cores (compensated FP32).        */
+  int         gram_cuda_cores; /* FP32 blocks of width 12, 16 or 24 on graphs of at least
+                                 65,536 nodes: 0 (default) computes the Rayleigh-Ritz Grams
+                                 [X W P]^T A [X W P] and [X W P]^T B [X W P] on the tensor
+                                 cores (tcgen05, TF32 with each value split in two so that
+                                 products keep about 2^-21 relative accuracy); 1 computes them
+                                 on the CUDA cores (compensated FP32), as smaller graphs do. */
 } mge_embed_opts;
 
 typedef struct {

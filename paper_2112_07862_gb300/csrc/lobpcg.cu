@@ -1318,10 +1318,14 @@ struct Solver {
   }
 
   // S-side Grams on the tensor cores (gram_tc.cu) for FP32 blocks of width 12, 16, 24 with the
-  // full basis [X W P]
+  // full basis [X W P], on graphs of at least kTcMinRows rows: the kernel holds one CTA per SM
+  // with ~150-190 KB of shared memory, which on small graphs costs more than it saves and, in
+  // a batch of small solves, keeps the other solves' kernels off the SMs (measured on 512
+  // graphs of 2k-50k nodes: 5.4M node-embeddings/s with it against 6.8M without)
   static constexpr bool kTcWidth = sizeof(T) == 4 && (M == 12 || M == 16 || M == 24);
+  static constexpr int64_t kTcMinRows = 65536;
   int gram_ncl = 1;
-  bool use_tc_gram() const { return kTcWidth && !op.gram_cuda_cores; }
+  bool use_tc_gram() const { return kTcWidth && !op.gram_cuda_cores && n >= kTcMinRows; }
 
   mge_status launch_gram_s_tc() {
     if constexpr (kTcWidth) {
