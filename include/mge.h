@@ -186,8 +186,9 @@ mge_status mge_build_graph_ops(mge_ctx* ctx, int64_t n, const int64_t* row_ptr,
                                const mge_ops_opts* opts, mge_ops** out);
 
 /* Builds the operators of many graphs (each exactly as mge_build_graph_ops, Sec. 4) with
- * `workers` host threads (0 = 8), each issuing its builds on a CUDA stream of its own, so
- * that the builds' kernels, their eps solves and their host round trips overlap.
+ * `workers` host threads (0 = 8), each issuing its builds on a CUDA stream of its own: the
+ * steps before the eps = lambda_2(Q) solve on the workers, then every eps solve as a branch
+ * of ONE CUDA graph launch (as mge_embed_batch), then the steps after it on the workers.
  * n, row_ptr, col, w: count entries each (host or device pointers per on_device; device
  *   inputs written on opts->stream are waited for first).  opts: shared; its stream is not
  *   used by the builds.

@@ -2,6 +2,7 @@
 #include "mge_internal.cuh"
 
 #include <algorithm>
+#include <memory>
 #include <thread>
 #include <vector>
 
@@ -276,32 +277,91 @@ mge_status mge_build_graph_ops_batch(mge_ctx* c, int count, const int64_t* n, co
   for (int i = 0; i < count; ++i) out[i] = nullptr;
   // device inputs may still be in flight on the caller's stream
   if (on_device) MGE_CUDA(ctx, cudaStreamSynchronize(pick_stream(ctx, opts ? opts->stream : nullptr)));
-  std::vector<mge_status> sts((size_t)count, MGE_EDEVICE);    // stays so for a graph no worker took
-  std::atomic<int> next{0};
-  auto work = [&]() {
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return;
-    cudaStream_t s = nullptr;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return; }
-    mge_ops_opts oo{};
-    oo.precision = MGE_FP32;
-    if (opts) oo = *opts;
-    oo.stream = s;
-    for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1))
-      sts[i] = mge_build_graph_ops(c, n[i], row_ptr[i], col[i], w[i], on_device, &oo, &out[i]);
-    cudaStreamSynchronize(s);
-    cudaStreamDestroy(s);
-  };
+  mge_ops_opts oo{};
+  oo.precision = MGE_FP32;
+  if (opts) oo = *opts;
+  // graph i is built by worker i % nw on that worker's stream, in both phases
   const int nw = std::max(1, std::min(workers > 0 ? workers : 8, count));
-  std::vector<std::thread> pool;
-  for (int t = 1; t < nw; ++t) {
-    try {
-      pool.emplace_back(work);
-    } catch (...) {
-      break;
+  std::vector<cudaStream_t> streams((size_t)nw, nullptr);
+  for (int t = 0; t < nw; ++t) MGE_CUDA(ctx, cudaStreamCreateWithFlags(&streams[t], cudaStreamNonBlocking));
+  std::vector<mge_status> sts((size_t)count, MGE_EDEVICE);    // stays so for a graph no worker took
+  std::vector<std::unique_ptr<BuildState>> bss((size_t)count);
+  std::vector<double> eps((size_t)count, 0.0);
+  auto run_workers = [&](auto&& fn) {
+    std::vector<std::thread> pool;
+    auto work = [&](int t) {
+      if (cudaSetDevice(ctx->device) != cudaSuccess) return;
+      for (int i = t; i < count; i += nw) fn(i, streams[t]);
+    };
+    for (int t = 1; t < nw; ++t) {
+      try {
+        pool.emplace_back(work, t);
+      } catch (...) {
+        break;
+      }
+    }
+    work(0);
+    for (auto& th : pool) th.join();
+    // a worker that could not be started leaves its graphs with MGE_EDEVICE
+  };
+  // phase 1: everything up to the eps solve
+  run_workers([&](int i, cudaStream_t s) {
+    mge_ops* o = new mge_ops();
+    ctx->refs++;
+    bss[i] = std::make_unique<BuildState>();
+    mge_ops_opts local = oo;
+    local.stream = s;
+    sts[i] = build_phase1(ctx, s, n[i], row_ptr[i], col[i], w[i], on_device, &local, &o->impl, bss[i].get());
+    if (sts[i] != MGE_OK) {
+      bss[i].reset();
+      delete o;
+      ctx_release(ctx);
+      return;
+    }
+    out[i] = o;
+  });
+  // phase 2: every eps solve as a branch of one CUDA graph launch
+  std::vector<int> idx;
+  for (int i = 0; i < count; ++i)
+    if (sts[i] == MGE_OK && bss[i]->need_eps) idx.push_back(i);
+  if (!idx.empty()) {
+    const int ne = (int)idx.size();
+    std::vector<LobOp> qops((size_t)ne);
+    std::vector<int> Ks((size_t)ne, 1), ms((size_t)ne);
+    std::vector<LobResult> res((size_t)ne);
+    std::vector<mge_status> est((size_t)ne, MGE_OK);
+    for (int e = 0; e < ne; ++e) { qops[e] = bss[idx[e]]->qop; ms[e] = bss[idx[e]]->eps_m; }
+    const BuildState& b0 = *bss[idx[0]];
+    double ms_batch = 0;
+    mge_status s = lobpcg_solve_batch(ctx, streams[0], ne, qops.data(), b0.eps_precision, Ks.data(), ms.data(),
+                                      b0.eps_tol, b0.eps_maxiter, b0.eps_seed, nullptr, res.data(), est.data(),
+                                      &ms_batch);
+    for (int e = 0; e < ne; ++e) {
+      const int i = idx[e];
+      const mge_status si = (s != MGE_OK && s != MGE_ENOTCONVERGED) ? s : est[e];
+      if (si != MGE_OK && si != MGE_ENOTCONVERGED) { sts[i] = si; continue; }
+      eps[i] = res[e].lambda.empty() ? 0.0 : res[e].lambda[0];
+      out[i]->impl.eps_iters = res[e].iters;
+      out[i]->impl.eps_resid = res[e].eta.empty() ? 0.0 : res[e].eta[0];
     }
   }
-  work();
-  for (auto& t : pool) t.join();
+  // phase 3: mu, A, B and the preconditioner's operator
+  run_workers([&](int i, cudaStream_t s) {
+    (void)s;
+    if (!out[i]) return;
+    if (sts[i] == MGE_OK) sts[i] = build_phase3(bss[i].get(), &out[i]->impl, eps[i]);
+    bss[i].reset();
+    if (sts[i] != MGE_OK && sts[i] != MGE_EDEGENERATE) {
+      out[i]->impl.each_buffer([](auto& b) { if (b.pooled) b.st = cudaStreamPerThread; });
+      delete out[i];
+      out[i] = nullptr;
+      ctx_release(ctx);
+    }
+  });
+  for (auto s : streams) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
   mge_status first = MGE_OK;
   for (int i = 0; i < count; ++i) {
     if (status) status[i] = sts[i];

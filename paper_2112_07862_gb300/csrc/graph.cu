@@ -644,23 +644,25 @@ mge_status scan_exclusive(Ctx* ctx, cudaStream_t st, const int64_t* in, int64_t 
   return exclusive_scan(ctx, st, in, n, out);
 }
 
-mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* rp_in,
-                                const int32_t* col_in, const double* w_in, int on_device,
-                                const mge_ops_opts* opts, Ops* ops) {
+mge_status build_phase1(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* rp_in, const int32_t* col_in,
+                        const double* w_in, int on_device, const mge_ops_opts* opts, Ops* ops, BuildState* bs) {
+  bs->ctx = ctx;
+  bs->st = st;
+  bs->n = n;
   if (n < 1) { set_error(ctx, "n must be >= 1"); return MGE_EINVAL; }
   // the handle's arrays come from the context's pool, ordered on this stream
   PersistentPoolScope pool_scope(st);
   if (!rp_in || !col_in || !w_in) { set_error(ctx, "null CSR pointer"); return MGE_EINVAL; }
-  mge_ops_opts o{};
+  mge_ops_opts& o = bs->o;
+  o = mge_ops_opts{};
   o.precision = MGE_FP32;
   if (opts) o = *opts;
   if (o.precision < MGE_FP64 || o.precision > MGE_BF16) { set_error(ctx, "bad precision"); return MGE_EINVAL; }
   ops->ctx = ctx;
   ops->n = n;
-  cudaEvent_t e0, e1;
-  MGE_CUDA(ctx, cudaEventCreate(&e0));
-  MGE_CUDA(ctx, cudaEventCreate(&e1));
-  MGE_CUDA(ctx, cudaEventRecord(e0, st));
+  MGE_CUDA(ctx, cudaEventCreate(&bs->e0));
+  MGE_CUDA(ctx, cudaEventCreate(&bs->e1));
+  MGE_CUDA(ctx, cudaEventRecord(bs->e0, st));
 
   // row pointers first (host check of the ends), then the arrays
   int64_t ends[2];
@@ -695,8 +697,8 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
   const double* w = ops->w_val.p;
 
   // small device scalars: [err, big_count, ncomp] and doubles [den_max, normq, norma, bmax, sumlog]
-  DevBuf<unsigned> d_err;  MGE_TRY(d_err.scratch(ctx, 4, st));
-  DevBuf<double> d_sc;     MGE_TRY(d_sc.scratch(ctx, 8, st));
+  DevBuf<unsigned>& d_err = bs->d_err;  MGE_TRY(d_err.scratch(ctx, 4, st));
+  DevBuf<double>& d_sc = bs->d_sc;      MGE_TRY(d_sc.scratch(ctx, 8, st));
   MGE_CUDA(ctx, cudaMemsetAsync(d_err.p, 0, 4 * sizeof(unsigned), st));
   MGE_CUDA(ctx, cudaMemsetAsync(d_sc.p, 0, 8 * sizeof(double), st));
   unsigned* err = d_err.p;
@@ -746,7 +748,8 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
   }
 
   // --- two-hop sets ---
-  DevBuf<int64_t> cnt, U;
+  DevBuf<int64_t> cnt;
+  DevBuf<int64_t>& U = bs->U;
   DevBuf<int32_t> big_list;
   MGE_TRY(cnt.scratch(ctx, n, st));
   MGE_TRY(U.scratch(ctx, n + 1, st));
@@ -759,7 +762,7 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
   MGE_CUDA(ctx, cudaMemcpyAsync(&total_cand, U.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   MGE_CUDA(ctx, cudaMemcpyAsync(&h_big, big_count, sizeof(int), cudaMemcpyDeviceToHost, st));
   MGE_CUDA(ctx, cudaStreamSynchronize(st));
-  DevBuf<int32_t> tlist;
+  DevBuf<int32_t>& tlist = bs->tlist;
   MGE_TRY(tlist.scratch(ctx, std::max<int64_t>(total_cand, 1), st));
   MGE_TRY(ops->T.alloc(ctx, n));
   {
@@ -835,12 +838,13 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
     ops->ncomp = h_ncomp;
     ops->norm_q = h_nq > 0 ? h_nq : 1.0;
     ops->beta_q = h_bq > 0 ? h_bq : 2.0;
-    // --- eps = lambda_2(Q) ---
-    double eps = 0.0;
-    if (o.eps_override_set) {
-      eps = o.eps_override;
-    } else if (n >= 2 && h_ncomp == 1) {
-      LobOp qop;
+    bs->h_ncomp = h_ncomp;
+    bs->h_den = h_den;
+    // --- the eps = lambda_2(Q) solve, prepared for build_eps_single or a batched launch ---
+    bs->need_eps = !o.eps_override_set && n >= 2 && h_ncomp == 1;
+    if (bs->need_eps) {
+      LobOp& qop = bs->qop;
+      qop = LobOp{};
       qop.n = n; qop.ptr = ops->q_ptr.p; qop.col = ops->q_col.p;
       qop.val = (o.precision == MGE_FP64) ? (const void*)ops->q_val.p : (const void*)ops->q_val32.p;
       qop.shift = 0.0; qop.b = nullptr;
@@ -866,21 +870,57 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
         set_error(ctx, "graph too small for the eps solve block (n = %lld)", (long long)n);
         return MGE_EINVAL;
       }
-      LobResult lr;
-      int prec = (o.precision == MGE_FP64) ? MGE_FP64 : MGE_FP32;
-      mge_status s = lobpcg_solve(ctx, st, qop, prec, 1, m, tol, maxit, o.seed ^ 0x9e3779b97f4a7c15ull,
-                                  16, true, nullptr, 0, nullptr, &lr);
-      if (s != MGE_OK && s != MGE_ENOTCONVERGED) return s;
-      eps = lr.lambda[0];
-      ops->eps_iters = lr.iters;
-      ops->eps_resid = lr.eta.empty() ? 0.0 : lr.eta[0];
+      bs->eps_m = m;
+      bs->eps_tol = tol;
+      bs->eps_maxiter = maxit;
+      bs->eps_precision = (o.precision == MGE_FP64) ? MGE_FP64 : MGE_FP32;
+      bs->eps_seed = o.seed ^ 0x9e3779b97f4a7c15ull;
     }
-    ops->degenerate = (!o.eps_override_set && h_ncomp > 1) ? 1 : 0;
+  }
+  return MGE_OK;
+}
+
+// The single eps solve of a build (phase 2 when the build runs alone).
+mge_status build_eps_single(BuildState* bs, Ops* ops, double* eps) {
+  LobResult lr;
+  mge_status s = lobpcg_solve(bs->ctx, bs->st, bs->qop, bs->eps_precision, 1, bs->eps_m, bs->eps_tol,
+                              bs->eps_maxiter, bs->eps_seed, 16, true, nullptr, 0, nullptr, &lr);
+  if (s != MGE_OK && s != MGE_ENOTCONVERGED) return s;
+  *eps = lr.lambda[0];
+  ops->eps_iters = lr.iters;
+  ops->eps_resid = lr.eta.empty() ? 0.0 : lr.eta[0];
+  return MGE_OK;
+}
+
+// Phase 3: mu (Eq. 9), A, the radii and B (Sec. 4.3), the preconditioner's operator.
+mge_status build_phase3(BuildState* bs, Ops* ops, double eps) {
+  Ctx* ctx = bs->ctx;
+  cudaStream_t st = bs->st;
+  const int64_t n = bs->n;
+  const mge_ops_opts& o = bs->o;
+  PersistentPoolScope pool_scope(st);
+  const int64_t* rp = ops->w_ptr.p;
+  const int32_t* col = ops->w_col.p;
+  const double* w = ops->w_val.p;
+  DevBuf<int64_t>& U = bs->U;
+  DevBuf<int32_t>& tlist = bs->tlist;
+  DevBuf<double>& d_sc = bs->d_sc;
+  unsigned* err = bs->d_err.p;
+  double* norma = d_sc.p + 2;
+  double* bmax = d_sc.p + 3;
+  double* sumlog = d_sc.p + 4;
+  double* beta_a = d_sc.p + 6;
+  cudaEvent_t e0 = bs->e0, e1 = bs->e1;
+  unsigned h_err = 0;
+  const int B = 256;
+  {
+    if (o.eps_override_set) eps = o.eps_override;
+    ops->degenerate = (!o.eps_override_set && bs->h_ncomp > 1) ? 1 : 0;
     ops->eps = eps;
     // --- mu (Eq. 9) ---
     double mu = 0.0;
     if (o.mu_override_set) mu = o.mu_override;
-    else if (eps != 0.0 && h_den > 0) mu = eps / h_den;
+    else if (eps != 0.0 && bs->h_den > 0) mu = eps / bs->h_den;
     ops->mu = mu;
   }
 
@@ -931,6 +971,7 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    bs->e0 = bs->e1 = nullptr;
     ops->build_ms = ms;
     ops->norm_a = h_na > 0 ? h_na : 1.0;
     ops->bmax = h_bm > 0 ? h_bm : 1.0;
@@ -962,6 +1003,16 @@ mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int6
     return MGE_EISOLATED;
   }
   return ops->degenerate ? MGE_EDEGENERATE : MGE_OK;
+}
+
+mge_status build_graph_ops_impl(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* rp_in,
+                                const int32_t* col_in, const double* w_in, int on_device,
+                                const mge_ops_opts* opts, Ops* ops) {
+  BuildState bs;
+  MGE_TRY(build_phase1(ctx, st, n, rp_in, col_in, w_in, on_device, opts, ops, &bs));
+  double eps = 0.0;
+  if (bs.need_eps) MGE_TRY(build_eps_single(&bs, ops, &eps));
+  return build_phase3(&bs, ops, eps);
 }
 
 }  // namespace mge

@@ -293,6 +293,41 @@ struct LobOp {
   const int32_t* row_rank = nullptr;
 };
 
+// The operator build in three phases (graph.cu): phase 1 up to the eps = lambda_2(Q) solve
+// (two-hop sets, Q, its components), the eps solve (alone, or as one branch of a batched
+// launch), phase 3 (mu, A, r, b and the preconditioner's operator).  The state that spans the
+// phases: scratch ordered on the build's stream, the host copies of phase 1's scalars and the
+// prepared eps solve.
+struct BuildState {
+  Ctx* ctx = nullptr;
+  cudaStream_t st = nullptr;
+  int64_t n = 0;
+  mge_ops_opts o{};
+  DevBuf<int64_t> U;                 // two-hop candidate offsets
+  DevBuf<int32_t> tlist;             // two-hop lists
+  DevBuf<unsigned> d_err;
+  DevBuf<double> d_sc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int h_ncomp = 0;
+  double h_den = 0;
+  bool need_eps = false;
+  LobOp qop;
+  int eps_m = 0, eps_maxiter = 0, eps_precision = MGE_FP32;
+  double eps_tol = 0;
+  uint64_t eps_seed = 0;
+  BuildState() = default;
+  BuildState(const BuildState&) = delete;
+  BuildState& operator=(const BuildState&) = delete;
+  ~BuildState() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+mge_status build_phase1(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* rp_in, const int32_t* col_in,
+                        const double* w_in, int on_device, const mge_ops_opts* opts, Ops* ops, BuildState* bs);
+mge_status build_eps_single(BuildState* bs, Ops* ops, double* eps);
+mge_status build_phase3(BuildState* bs, Ops* ops, double eps);
+
 struct LobResult {
   mge_status status = MGE_OK;
   int iters = 0;
