@@ -694,6 +694,7 @@ static LobOp make_op(const Ops& op, int which, int precision) {
     l.b = dbl ? (const void*)op.b.p : (const void*)op.b32.p;
     l.dinv = dbl ? (const void*)op.dinv_a.p : (const void*)op.dinv_a32.p;
     l.norm = op.norm_a; l.bmax = op.bmax; l.deflate = false; l.beta = op.beta_a;
+    l.nnz = op.nnz_a;
     // the preconditioner approximates A^-1 through L + eps I: mu Q moves only the bottom of
     // the spectrum, by O(eps), and W has far fewer nonzeros than A
     if (op.l_val.p) {
@@ -702,6 +703,7 @@ static LobOp make_op(const Ops& op, int which, int precision) {
       l.pc_shift = op.eps;
       l.pc_dinv = dbl ? (const void*)op.l_dinv.p : (const void*)op.l_dinv32.p;
       l.pc_beta = op.beta_l;
+      l.pc_nnz = op.nnz_w;
       if (op.l_sl.built()) {
         l.sl_slp = op.l_sl.slp.p; l.sl_perm = op.l_sl.perm.p; l.sl_col = op.l_sl.col.p;
         l.sl_val = dbl ? (const void*)op.l_sl.val.p : (const void*)op.l_sl.val32.p;
@@ -714,6 +716,7 @@ static LobOp make_op(const Ops& op, int which, int precision) {
     l.shift = 0.0; l.b = nullptr;
     l.dinv = dbl ? (const void*)op.dinv_q.p : (const void*)op.dinv_q32.p;
     l.norm = op.norm_q; l.bmax = 1.0; l.deflate = true; l.beta = op.beta_q;
+    l.nnz = op.nnz_q;
     if (op.q_sl.built()) {
       l.sl_slp = op.q_sl.slp.p; l.sl_perm = op.q_sl.perm.p; l.sl_col = op.q_sl.col.p;
       l.sl_val = dbl ? (const void*)op.q_sl.val.p : (const void*)op.q_sl.val32.p;
@@ -816,7 +819,7 @@ mge_status mge_embed(mge_ctx* c, const mge_ops* o, int K, double tol, const mge_
     else { MGE_TRY(vd.scratch(ctx, (size_t)op.n * K, st)); vout = vd.p; }
   }
   LobResult r;
-  l.precond_degree = e.precond_degree > 0 ? std::min(e.precond_degree, 64) : kDefaultPrecondDegree;
+  l.precond_degree = e.precond_degree > 0 ? std::min(e.precond_degree, 64) : default_precond_degree(op.n);
   if (bf16) l.precond_degree = std::min(l.precond_degree, kBf16MaxPrecondDegree);
   l.rr_fp64 = rr_fp64_for(e, prec);
   l.gram_cuda_cores = e.gram_cuda_cores != 0;
@@ -873,7 +876,7 @@ mge_status mge_embed_batch(mge_ctx* c, int count, const mge_ops* const* ops, con
     if (op.n < 2 * m) { set_error(ctx, "embed_batch: graph %d has %lld nodes; need at least %d", i, (long long)op.n, 2 * m); return MGE_EINVAL; }
     ms[i] = m;
     lops[i] = make_op(op, 0, prec);
-    lops[i].precond_degree = e.precond_degree > 0 ? std::min(e.precond_degree, 64) : kDefaultPrecondDegree;
+    lops[i].precond_degree = e.precond_degree > 0 ? std::min(e.precond_degree, 64) : default_precond_degree(op.n);
     if (bf16) lops[i].precond_degree = std::min(lops[i].precond_degree, kBf16MaxPrecondDegree);
     lops[i].rr_fp64 = rr_fp64_for(e, prec);
     lops[i].pc_bf16 = bf16;

@@ -850,7 +850,8 @@ mge_status build_phase1(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* rp_
       qop.shift = 0.0; qop.b = nullptr;
       qop.dinv = (o.precision == MGE_FP64) ? (const void*)ops->dinv_q.p : (const void*)ops->dinv_q32.p;
       qop.norm = ops->norm_q; qop.bmax = 1.0; qop.deflate = true; qop.beta = ops->beta_q;
-      qop.precond_degree = o.eps_precond_degree > 0 ? std::min(o.eps_precond_degree, 64) : kDefaultEpsPrecondDegree;
+      qop.precond_degree = o.eps_precond_degree > 0 ? std::min(o.eps_precond_degree, 64) : default_eps_precond_degree(n);
+      qop.nnz = ops->nnz_q;
       qop.rr_fp64 = o.precision == MGE_FP64;
       qop.pc_bf16 = o.precision == MGE_BF16;
       if (qop.pc_bf16) qop.precond_degree = std::min(qop.precond_degree, kBf16MaxPrecondDegree);

@@ -1593,14 +1593,21 @@ mge_status prepare_solver(Solver<T, M>& s) {
   cudaStream_t st = s.st;
   const LobOp& op = s.op;
   MGE_TRY(s.setup());
-  int64_t nnz = 0;
-  MGE_CUDA(ctx, cudaMemcpyAsync(&nnz, op.ptr + op.n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  // entry counts from the host copy when the caller has them (no device round trip, so that a
+  // batch can prepare its next solves while earlier ones run)
+  int64_t nnz = op.nnz;
+  if (nnz < 0) {
+    MGE_CUDA(ctx, cudaMemcpyAsync(&nnz, op.ptr + op.n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    MGE_CUDA(ctx, cudaStreamSynchronize(st));
+  }
   s.nnz_a = nnz;
   s.nnz_pc = nnz;
   if (op.pc_ptr) {
-    MGE_CUDA(ctx, cudaMemcpyAsync(&s.nnz_pc, op.pc_ptr + op.n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    MGE_CUDA(ctx, cudaStreamSynchronize(st));
+    s.nnz_pc = op.pc_nnz;
+    if (s.nnz_pc < 0) {
+      MGE_CUDA(ctx, cudaMemcpyAsync(&s.nnz_pc, op.pc_ptr + op.n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+      MGE_CUDA(ctx, cudaStreamSynchronize(st));
+    }
   }
   MGE_CUDA(ctx, cudaFuncSetAttribute(k_gram<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
   MGE_CUDA(ctx, (spmm_configure<T, M>()));
@@ -1742,17 +1749,12 @@ mge_status lobpcg_solve_batch(Ctx* ctx, cudaStream_t st, int count, const LobOp*
     if (!it) { set_error(ctx, "batch item %d: unsupported block width %d", i, m[i]); return MGE_EINVAL; }
     items.emplace_back(it);
   }
-  for (auto& it : items) MGE_TRY(it->prepare());
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  MGE_CUDA(ctx, cudaGraphCreate(&graph, 0));
-  for (auto& it : items) {
-    const mge_status a = it->add(graph, seed);
-    if (a != MGE_OK) { cudaGraphDestroy(graph); return a; }
-  }
-  const cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (ie != cudaSuccess) { set_error(ctx, "batch graph instantiation: %s", cudaGetErrorString(ie)); return MGE_EDEVICE; }
+  // The solves go out in chunks of kChunk: each chunk is prepared (allocations and set-up on
+  // st, which nothing else uses meanwhile), captured as one graph with a branch per solve,
+  // instantiated and launched on one of kLanes streams, so that the host work of the next chunk
+  // overlaps the device work of the launched ones (instantiating one graph of hundreds of
+  // solves took longer than much of their device time).
+  constexpr int kChunk = 64, kLanes = 4;
   State* hst = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   mge_status out = MGE_OK;
@@ -1761,11 +1763,56 @@ mge_status lobpcg_solve_batch(Ctx* ctx, cudaStream_t st, int count, const LobOp*
     out = MGE_EDEVICE;
   };
   cudaError_t e;
+  std::vector<cudaStream_t> lanes;
+  std::vector<cudaGraphExec_t> execs;
+  std::vector<cudaEvent_t> evs;
+  auto new_event = [&]() -> cudaEvent_t {
+    cudaEvent_t ev = nullptr;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) { fail(e, "cudaEventCreate"); return nullptr; }
+    evs.push_back(ev);
+    return ev;
+  };
   if ((e = cudaMallocHost(&hst, sizeof(State) * (size_t)count)) != cudaSuccess) fail(e, "cudaMallocHost");
   if (out == MGE_OK && (e = cudaEventCreate(&e0)) != cudaSuccess) fail(e, "cudaEventCreate");
   if (out == MGE_OK && (e = cudaEventCreate(&e1)) != cudaSuccess) fail(e, "cudaEventCreate");
-  if (out == MGE_OK && (e = cudaEventRecord(e0, st)) != cudaSuccess) fail(e, "cudaEventRecord");
-  if (out == MGE_OK && (e = cudaGraphLaunch(gexec, st)) != cudaSuccess) fail(e, "cudaGraphLaunch");
+  for (int l = 0; l < kLanes && out == MGE_OK; ++l) {
+    cudaStream_t s = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) fail(e, "cudaStreamCreate");
+    else lanes.push_back(s);
+  }
+  for (int c0 = 0, lane = 0; c0 < count && out == MGE_OK; c0 += kChunk, lane = (lane + 1) % kLanes) {
+    const int c1 = std::min(count, c0 + kChunk);
+    for (int i = c0; i < c1 && out == MGE_OK; ++i) {
+      const mge_status p = items[i]->prepare();
+      if (p != MGE_OK) out = p;
+    }
+    if (out != MGE_OK) break;
+    cudaGraph_t graph = nullptr;
+    if ((e = cudaGraphCreate(&graph, 0)) != cudaSuccess) { fail(e, "cudaGraphCreate"); break; }
+    for (int i = c0; i < c1 && out == MGE_OK; ++i) {
+      const mge_status a = items[i]->add(graph, seed);
+      if (a != MGE_OK) out = a;
+    }
+    cudaGraphExec_t gexec = nullptr;
+    if (out == MGE_OK && (e = cudaGraphInstantiate(&gexec, graph, 0)) != cudaSuccess) fail(e, "batch graph instantiation");
+    cudaGraphDestroy(graph);
+    if (out != MGE_OK) break;
+    execs.push_back(gexec);
+    // the chunk's buffers were allocated and set up on st
+    if (c0 == 0 && (e = cudaEventRecord(e0, st)) != cudaSuccess) { fail(e, "cudaEventRecord"); break; }
+    cudaEvent_t ready = new_event();
+    if (!ready) break;
+    if ((e = cudaEventRecord(ready, st)) != cudaSuccess) { fail(e, "cudaEventRecord"); break; }
+    if ((e = cudaStreamWaitEvent(lanes[lane], ready, 0)) != cudaSuccess) { fail(e, "cudaStreamWaitEvent"); break; }
+    if ((e = cudaGraphLaunch(gexec, lanes[lane])) != cudaSuccess) { fail(e, "cudaGraphLaunch"); break; }
+  }
+  // join the lanes back into st
+  for (cudaStream_t s : lanes) {
+    cudaEvent_t done = new_event();
+    if (!done) break;
+    if ((e = cudaEventRecord(done, s)) != cudaSuccess) { fail(e, "cudaEventRecord"); break; }
+    if ((e = cudaStreamWaitEvent(st, done, 0)) != cudaSuccess) { fail(e, "cudaStreamWaitEvent"); break; }
+  }
   if (out == MGE_OK && (e = cudaEventRecord(e1, st)) != cudaSuccess) fail(e, "cudaEventRecord");
   for (int i = 0; i < count && out == MGE_OK; ++i)
     if ((e = cudaMemcpyAsync(&hst[i], items[i]->device_state(), sizeof(State), cudaMemcpyDeviceToHost, st)) !=
@@ -1786,10 +1833,13 @@ mge_status lobpcg_solve_batch(Ctx* ctx, cudaStream_t st, int count, const LobOp*
     }
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) fail(e, "batch results");
   }
+  for (cudaStream_t s : lanes) cudaStreamSynchronize(s);
+  for (cudaGraphExec_t x : execs) cudaGraphExecDestroy(x);
+  for (cudaStream_t s : lanes) cudaStreamDestroy(s);
+  for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (hst) cudaFreeHost(hst);
-  cudaGraphExecDestroy(gexec);
   return out;
 }
 

@@ -7,6 +7,7 @@
 #include <stdio.h>
 
 #include <atomic>
+#include <cmath>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -250,6 +251,18 @@ mge_status betweenness_run(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* 
 // solve converges in about 23 iterations at 24)
 constexpr int kDefaultPrecondDegree = 64;
 constexpr int kDefaultEpsPrecondDegree = 24;
+// Defaults by graph size.  The best degree grows with n (the spectrum to flatten widens as the
+// smallest eigenvalues shrink): measured best embedding degree 24 on graphs of 2k-50k nodes
+// (512-graph batch: 8.3M node-embeddings/s at 24, 6.9M at 48, 5.7M at 64) and 64 at 200k;
+// best eps-solve degree 8-12 on the small graphs, 32 at 200k and at 2M.
+inline int default_precond_degree(int64_t n) {
+  const int d = (int)std::lround(std::sqrt((double)n) / 5.0);
+  return d < 16 ? 16 : d > kDefaultPrecondDegree ? kDefaultPrecondDegree : d;
+}
+inline int default_eps_precond_degree(int64_t n) {
+  const int d = (int)std::lround(std::sqrt((double)n) / 12.0);
+  return d < 8 ? 8 : d > 32 ? 32 : d;
+}
 // BF16 preconditioner blocks: the Chebyshev polynomial amplifies the bottom of the spectrum by
 // about 2 d^2 against the top, so BF16 rounding (u = 2^-8) of its iterates leaves the
 // preconditioned block with an O(1) relative error in the directions LOBPCG needs once
@@ -259,6 +272,8 @@ constexpr int kBf16MaxPrecondDegree = 8;
 
 struct LobOp {
   int64_t n = 0;
+  int64_t nnz = -1, pc_nnz = -1;   // entries of the operator and of the preconditioner's (-1: read
+                                   // from the row pointers on the device)
   const int64_t* ptr = nullptr;
   const int32_t* col = nullptr;
   const void* val = nullptr;       // double* or float* by precision
