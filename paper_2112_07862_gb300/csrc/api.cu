@@ -270,6 +270,7 @@ mge_status mge_build_graph_ops(mge_ctx* c, int64_t n, const int64_t* row_ptr, co
 mge_status mge_build_graph_ops_batch(mge_ctx* c, int count, const int64_t* n, const int64_t* const* row_ptr,
                                      const int32_t* const* col, const double* const* w, int on_device,
                                      const mge_ops_opts* opts, int workers, mge_ops** out, mge_status* status) {
+  NvtxRange nvtx_range("mge.build_batch");
   if (!c || count < 1 || !n || !row_ptr || !col || !w || !out) return MGE_EINVAL;
   Ctx* ctx = &c->impl;
   if (ctx->closed) return MGE_EINVAL;
@@ -521,6 +522,7 @@ mge_status mge_ops_node_order(const mge_ops* o, int32_t* order, int on_device) {
 
 mge_status mge_knn_graph(mge_ctx* c, int64_t n, int dim, const double* points, int on_device, int k,
                          void* stream, mge_graph** out) {
+  NvtxRange nvtx_range("mge.knn_graph");
   if (!c || !out || !points) return MGE_EINVAL;
   *out = nullptr;
   Ctx* ctx = &c->impl;
@@ -607,6 +609,7 @@ mge_status mge_graph_destroy(mge_graph* g) {
 
 mge_status mge_betweenness(mge_ctx* c, int64_t n, const int64_t* row_ptr, const int32_t* col, int on_device,
                            double* cb, double* vbc, void* stream) {
+  NvtxRange nvtx_range("mge.betweenness");
   if (!c || !row_ptr || !cb || n < 1) return MGE_EINVAL;
   Ctx* ctx = &c->impl;
   if (ctx->closed) return MGE_EINVAL;
@@ -643,6 +646,7 @@ mge_status mge_betweenness(mge_ctx* c, int64_t n, const int64_t* row_ptr, const 
 
 mge_status mge_kmeans(mge_ctx* c, int64_t n, int K, const double* X, int C, const double* centres0, int max_iters,
                       int on_device, int32_t* assign, double* centres, int* iters, void* stream) {
+  NvtxRange nvtx_range("mge.kmeans");
   if (!c || !X || !centres0 || !assign || !centres) return MGE_EINVAL;
   Ctx* ctx = &c->impl;
   if (ctx->closed) return MGE_EINVAL;
@@ -770,6 +774,7 @@ mge_status mge_ops_apply_inplace(mge_ctx* c, const mge_ops* o, int which, int pr
 
 mge_status mge_embed(mge_ctx* c, const mge_ops* o, int K, double tol, const mge_embed_opts* opts,
                      double* lambda, void* V, mge_embed_info* info) {
+  NvtxRange nvtx_range("mge.embed");
   if (!c || !o || !lambda) return MGE_EINVAL;
   if (c->impl.closed) return MGE_EINVAL;
   Ctx* ctx = &c->impl;
@@ -848,6 +853,7 @@ mge_status mge_embed(mge_ctx* c, const mge_ops* o, int K, double tol, const mge_
 mge_status mge_embed_batch(mge_ctx* c, int count, const mge_ops* const* ops, const int* K, double tol,
                            const mge_embed_opts* opts, double* const* lambda, void* const* V,
                            mge_embed_info* info) {
+  NvtxRange nvtx_range("mge.embed_batch");
   if (!c || count < 1 || !ops || !K || !lambda) return MGE_EINVAL;
   if (c->impl.closed) return MGE_EINVAL;
   Ctx* ctx = &c->impl;

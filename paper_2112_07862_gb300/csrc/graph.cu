@@ -646,6 +646,7 @@ mge_status scan_exclusive(Ctx* ctx, cudaStream_t st, const int64_t* in, int64_t 
 
 mge_status build_phase1(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* rp_in, const int32_t* col_in,
                         const double* w_in, int on_device, const mge_ops_opts* opts, Ops* ops, BuildState* bs) {
+  NvtxRange range("mge.build.two_hop_and_Q");
   bs->ctx = ctx;
   bs->st = st;
   bs->n = n;
@@ -883,6 +884,7 @@ mge_status build_phase1(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* rp_
 
 // The single eps solve of a build (phase 2 when the build runs alone).
 mge_status build_eps_single(BuildState* bs, Ops* ops, double* eps) {
+  NvtxRange range("mge.build.eps_solve");
   LobResult lr;
   mge_status s = lobpcg_solve(bs->ctx, bs->st, bs->qop, bs->eps_precision, 1, bs->eps_m, bs->eps_tol,
                               bs->eps_maxiter, bs->eps_seed, 16, true, nullptr, 0, nullptr, &lr);
@@ -895,6 +897,7 @@ mge_status build_eps_single(BuildState* bs, Ops* ops, double* eps) {
 
 // Phase 3: mu (Eq. 9), A, the radii and B (Sec. 4.3), the preconditioner's operator.
 mge_status build_phase3(BuildState* bs, Ops* ops, double eps) {
+  NvtxRange range("mge.build.mu_A_B");
   Ctx* ctx = bs->ctx;
   cudaStream_t st = bs->st;
   const int64_t n = bs->n;

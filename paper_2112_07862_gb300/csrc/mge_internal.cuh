@@ -13,9 +13,21 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mge.h"
 
 namespace mge {
+
+// A named range on the NVTX timeline (header-only NVTX 3: inert unless a profiler is attached)
+// around each phase of a call, so that a timeline shows build, eps solve, embedding, kNN,
+// k-means and betweenness as separate spans.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------------------------------
 // error plumbing: every CUDA call is checked and turned into an mge_status
