@@ -298,12 +298,20 @@ typedef struct {
                                  count about in proportion.  The paper leaves the
                                  preconditioner open.  0 = default 64; at most 64.          */
   int         rr_fp64;        /* arithmetic of the Rayleigh-Ritz eigensolve and of the
-                                 Cholesky that B-normalises W, for FP32 blocks: 0 (default)
-                                 the inverse-pencil FP32 solve described under MGE_FP32;
-                                 1 cyclic Jacobi on the 3m x 3m pencil in FP64.  Measured on a
-                                 200k-node swiss roll (K = 8, m = 16, tol 1e-5): FP32 27
-                                 iterations, 1.8 ms each; FP64 36 iterations, 3.6 ms each;
-                                 eigenvalues within 1e-6 of the oracle either way.  FP64
+                                 Cholesky that B-normalises W, for FP32 blocks:
+                                  0 (default) the inverse-pencil FP32 solve described under
+                                    MGE_FP32 until the largest relative residual of the K
+                                    wanted pairs has not halved for 10 iterations, then
+                                    cyclic Jacobi in FP64 for the rest of the solve;
+                                  1 cyclic Jacobi on the 3m x 3m pencil in FP64 throughout;
+                                 -1 the FP32 form throughout.
+                                 Measured on one GB300 (tol 1e-5): 200k-node swiss roll,
+                                 K = 8, m = 16: FP32 21 iterations at 2.1 ms, FP64 23 at
+                                 4.0 ms; 2M-node sphere, K = 16, m = 24: FP32 stalls at
+                                 relative residuals of 1-2e-5 (its eigenvectors carry errors
+                                 of about u times the pencil's spread, and the sphere's
+                                 eigenvalues come in near-degenerate groups), FP64 90
+                                 iterations.  info.rr_fp64_from reports which ran.  FP64
                                  blocks always use FP64.                                    */
   int         gram_cuda_cores; /* FP32 blocks of width 12, 16 or 24 on graphs of at least
                                  65,536 nodes: 0 (default) computes the Rayleigh-Ritz Grams
@@ -320,6 +328,8 @@ typedef struct {
   int    drops;               /* iterations whose Rayleigh-Ritz basis dropped a direction   */
   double resid[64];           /* relative residual rho_k of each returned pair (k < K)      */
   double solve_ms;            /* device time of the solve                                  */
+  int    rr_fp64_from;        /* Rayleigh-Ritz in FP64: -1 never, 0 from the start, k > 0
+                                 after iteration k (mge_embed_opts.rr_fp64)                 */
 } mge_embed_info;
 
 /* Fills lambda[K] (host, ascending) and V (column-major [n x K] FP64, host or device per

@@ -89,7 +89,7 @@ static cudaStream_t pick_stream(Ctx* ctx, void* s) {
 // Arithmetic of the Rayleigh-Ritz eigensolve and of W's Cholesky for reduced-precision
 // blocks: FP64 when opts.rr_fp64 is set (FP64 blocks always)
 static bool rr_fp64_for(const mge_embed_opts& e, int prec) {
-  return prec == MGE_FP64 || e.rr_fp64 != 0;
+  return prec == MGE_FP64 || e.rr_fp64 > 0;
 }
 
 // Extra LOBPCG columns beyond K: opts.guard > 0 as given, < 0 none, 0 the default of K more
@@ -824,9 +824,10 @@ mge_status mge_embed(mge_ctx* c, const mge_ops* o, int K, double tol, const mge_
     else { MGE_TRY(vd.scratch(ctx, (size_t)op.n * K, st)); vout = vd.p; }
   }
   LobResult r;
-  l.precond_degree = e.precond_degree > 0 ? std::min(e.precond_degree, 64) : default_precond_degree(op.n);
+  l.precond_degree = e.precond_degree > 0 ? std::min(e.precond_degree, kMaxPrecondDegree) : default_precond_degree(op.n);
   if (bf16) l.precond_degree = std::min(l.precond_degree, kBf16MaxPrecondDegree);
   l.rr_fp64 = rr_fp64_for(e, prec);
+  l.rr_switch = e.rr_fp64 == 0;
   l.gram_cuda_cores = e.gram_cuda_cores != 0;
   mge_status s = lobpcg_solve(ctx, st, l, prec, K, m, tol, e.maxiter, e.seed, e.check_every, e.use_graph != 0,
                               x0, x0c, vout, &r);
@@ -844,6 +845,7 @@ mge_status mge_embed(mge_ctx* c, const mge_ops* o, int K, double tol, const mge_
     info->iters = r.iters;
     info->m = m;
     info->drops = r.drops;
+    info->rr_fp64_from = r.rr64_from;
     for (int k = 0; k < 64; ++k) info->resid[k] = k < K ? r.eta[k] : 0.0;
     info->solve_ms = r.ms;
   }
@@ -882,9 +884,10 @@ mge_status mge_embed_batch(mge_ctx* c, int count, const mge_ops* const* ops, con
     if (op.n < 2 * m) { set_error(ctx, "embed_batch: graph %d has %lld nodes; need at least %d", i, (long long)op.n, 2 * m); return MGE_EINVAL; }
     ms[i] = m;
     lops[i] = make_op(op, 0, prec);
-    lops[i].precond_degree = e.precond_degree > 0 ? std::min(e.precond_degree, 64) : default_precond_degree(op.n);
+    lops[i].precond_degree = e.precond_degree > 0 ? std::min(e.precond_degree, kMaxPrecondDegree) : default_precond_degree(op.n);
     if (bf16) lops[i].precond_degree = std::min(lops[i].precond_degree, kBf16MaxPrecondDegree);
     lops[i].rr_fp64 = rr_fp64_for(e, prec);
+    lops[i].rr_switch = e.rr_fp64 == 0;
     lops[i].pc_bf16 = bf16;
     lops[i].gram_cuda_cores = e.gram_cuda_cores != 0;
   }
@@ -914,6 +917,7 @@ mge_status mge_embed_batch(mge_ctx* c, int count, const mge_ops* const* ops, con
       info[i].iters = res[i].iters;
       info[i].m = ms[i];
       info[i].drops = res[i].drops;
+      info[i].rr_fp64_from = res[i].rr64_from;
       for (int k = 0; k < 64; ++k) info[i].resid[k] = (k < K[i] && k < (int)res[i].eta.size()) ? res[i].eta[k] : 0.0;
       info[i].solve_ms = ms_batch;
     }

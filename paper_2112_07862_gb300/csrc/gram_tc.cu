@@ -4,11 +4,15 @@
 // as one MMA chain per CTA, D[128 x N] += A[128 x 32] B[N x 32]^T per tile of 32 rows,
 // with A = S^T (rows 3m..127 unused) and B = [AS | BS]^T (N = 6m rounded up to 16).
 //
-// FP32 accuracy from TF32 tensor cores: every FP32 value x is split into hi (x with the low
-// 13 mantissa bits cleared: exactly representable in TF32) and lo = x - hi (exact in FP32);
-// each tile issues hi*hi + hi*lo + lo*hi, so a product carries about 2^-21 relative error
-// instead of TF32's 2^-11.  The accumulator lives in tensor memory (FP32) for the CTA's rows
-// and is reduced across CTAs in FP64.
+// FP32 accuracy from TF32 tensor cores: every FP32 value x is split into hi = x rounded to
+// TF32 (to nearest) and lo = x - hi (exact in FP32) rounded to TF32; each tile issues
+// hi*hi + hi*lo + lo*hi, so a product carries about 2^-22 relative error, unbiased, instead
+// of TF32's 2^-11.  Sums: the tensor-memory accumulator (FP32) runs over a few tiles only
+// (TcShape::GROUP); the consumer warps then drain it into FP32 sums held in registers
+// (Kahan-compensated where they fit) while the next run accumulates in a second
+// tensor-memory region.  A single FP32 accumulator over all of a CTA's rows (13,000 at
+// n = 2M) put an error of ~8e-6 relative into the Ritz values, which floored the relative
+// residual just under a 1e-5 tolerance.  The CTAs' sums are reduced in FP64.
 //
 // Per CTA: a producer warp streams each tile's six 32 x m block slices and the 32 b_i into a
 // ring of three shared-memory stages with 1-D bulk copies (TMA); eight consumer warps split
@@ -16,9 +20,11 @@
 // (8-row x 16-byte core matrices: element (row r, k) at (r/8)*1024 + (k/4)*128 + (r%8)*16 +
 // (k%4)*4), into one of two operand buffers; one thread issues the twelve MMAs of the tile and
 // commits them to the buffer's mbarrier, which the consumers wait on before refilling it.
-// The epilogue reads the accumulator back (tcgen05.ld); the eight CTAs of a cluster add their
-// FP64 copies through distributed shared memory (each rank a slice of the entries) and add
-// the cluster's sums into the Gram accumulators with FP64 atomics.
+// A drain reads the accumulator back (tcgen05.ld.32x32b: warp w reads tensor-memory lanes
+// 32 (w % 4) .. + 31, i.e. Gram rows, and column half w / 4).  The epilogue writes the
+// compensated sums to shared memory in FP64; the eight CTAs of a cluster add their copies
+// through distributed shared memory (each rank a slice of the entries) and add the cluster's
+// sums into the Gram accumulators with FP64 atomics.
 #include "lobpcg_common.cuh"
 
 namespace mge {
@@ -45,7 +51,20 @@ struct TcShape {
   static constexpr int HDR = 1024;
   static constexpr int SMEM = HDR + kNRaw * RAW + 2 * BUF;
   static constexpr int TMEM_COLS = NMMA <= 32 ? 32 : NMMA <= 64 ? 64 : NMMA <= 128 ? 128 : 256;
+  static constexpr int TMEM_ALLOC = 2 * TMEM_COLS;                // two accumulator regions
+  static constexpr int H0 = (NB / 2 + 7) / 8 * 8;                 // columns of half 0 (x8 loads)
+  static constexpr int H1 = NB - H0;
+  static constexpr int QUARTERS = (NS + 31) / 32;                 // lane quarters holding rows
+  // Register sums: compensated (Kahan) where two floats per column fit the 168 registers a
+  // thread gets at 288 threads per CTA (m <= 16), plain FP32 at m = 24.  Run length: the error
+  // of the sums grows about as sqrt(runs) (plain) while that of a run grows with its length,
+  // so the plain sums take longer runs.
+  static constexpr bool KAHAN = M <= 16;
+  static constexpr int GROUP = KAHAN ? 4 : 8;                    // tiles per accumulation run
+  static constexpr int NC = KAHAN ? H0 : 1;                      // compensation terms
+  static_assert(GROUP >= 2, "a region is drained two tiles after its run ends");
   static_assert(NS <= 128 && NMMA <= 256, "Gram shape exceeds one MMA");
+  static_assert(H1 > 0 && H1 % 8 == 0 && H0 >= H1, "column halves");
   static_assert(NS * NB * 8 <= 2 * BUF, "epilogue does not fit the operand buffers");
 };
 
@@ -67,9 +86,45 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, 
                ::"r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
 }
 
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
-  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-  lo = x - hi;
+  hi = tf32_rna(x);
+  lo = tf32_rna(__fsub_rn(x, hi));     // x - hi is exact: it holds x's low 13 bits
+}
+
+// Kahan summation: s + (-c) carries the sum with the rounding errors of its additions
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  const float y = __fsub_rn(v, c);
+  const float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
+}
+
+// Adds one accumulator region into this thread's register sums: its lane (a Gram row) and W
+// columns from taddr on.  Warp-collective (tcgen05.ld .sync.aligned).
+template <int W, bool KAHAN, int NA, int NCA>
+__device__ __forceinline__ void tc_drain(uint32_t taddr, float (&s)[NA], float (&c)[NCA]) {
+  static_assert(W <= NA && W % 8 == 0 && (!KAHAN || W <= NCA), "drain width");
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+  for (int c0 = 0; c0 < W; c0 += 8) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr + (uint32_t)c0));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if constexpr (KAHAN) kahan_add(s[c0 + j], c[c0 + j], __uint_as_float(r[j]));
+      else s[c0 + j] = __fadd_rn(s[c0 + j], __uint_as_float(r[j]));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 
 template <int M>
@@ -99,7 +154,7 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 ::"r"(smem_u32(tmem_slot)), "r"(Sh::TMEM_COLS) : "memory");
+                 ::"r"(smem_u32(tmem_slot)), "r"(Sh::TMEM_ALLOC) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -110,6 +165,22 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
 
   const int64_t ntiles = (a.n + kTcT - 1) / kTcT;
   const int64_t my_tiles = active && blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  // compensated sums of this thread's Gram row (lane) over its warp's column half
+  const int quarter = warp & 3, half = warp >> 2;
+  const bool drainer = warp < kTcConsumers / 32 && quarter < Sh::QUARTERS;
+  float ks_s[Sh::H0], ks_c[Sh::NC];
+#pragma unroll
+  for (int j = 0; j < Sh::H0; ++j) ks_s[j] = 0.f;
+#pragma unroll
+  for (int j = 0; j < Sh::NC; ++j) ks_c[j] = 0.f;
+  // region (g & 1) holds run g; warp-uniform
+  auto drain = [&](int64_t g) {
+    if (!drainer) return;
+    const uint32_t addr = tmem + (uint32_t)((g & 1) * Sh::TMEM_COLS) + ((uint32_t)(32 * quarter) << 16) +
+                          (uint32_t)(half ? Sh::H0 : 0);
+    if (half == 0) tc_drain<Sh::H0, Sh::KAHAN>(addr, ks_s, ks_c);
+    else tc_drain<Sh::H1, Sh::KAHAN>(addr, ks_s, ks_c);
+  };
 
   if (warp == kTcConsumers / 32) {
     // ---------------- producer ----------------
@@ -136,6 +207,7 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(Sh::NMMA >> 3) << 17) |
                            ((uint32_t)(128 >> 4) << 24);
     int64_t issued = 0;                 // tiles whose MMAs were issued (the same in every consumer)
+    int64_t drained = 0;                // runs drained (the same in every consumer)
     for (int64_t i = 0; i < my_tiles; ++i) {
       const int s = (int)(i % kNRaw), buf = (int)(i & 1);
       const int64_t r0 = (blockIdx.x + i * gridDim.x) * kTcT;
@@ -186,16 +258,24 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
       asm volatile("bar.sync 1, %0;" ::"r"(kTcConsumers) : "memory");
       if (*reinterpret_cast<volatile int*>(s_fail)) break;      // uniform: set before the barrier
       ++issued;
+      // a run that ended with tile i - 2 is complete (every consumer waited for that tile's
+      // commit above); its region is next written by run g + 2, after later barriers
+      if (i >= 2 && (i - 2) % Sh::GROUP == Sh::GROUP - 1) {
+        drain((i - 2) / Sh::GROUP);
+        drained = (i - 2) / Sh::GROUP + 1;
+      }
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+        const uint32_t dt = tmem + (uint32_t)(((i / Sh::GROUP) & 1) * Sh::TMEM_COLS);
+        const bool first = i % Sh::GROUP == 0;
 #pragma unroll
         for (int ks = 0; ks < kTcT / 8; ++ks) {
           const uint32_t o = (uint32_t)ks * 2u * kLBO;
-          const uint32_t acc = (i == 0 && ks == 0) ? 0u : 1u;
-          mma_tf32(tmem, smem_desc(ah + o), smem_desc(bh + o), idesc, acc);
-          mma_tf32(tmem, smem_desc(ah + o), smem_desc(bl + o), idesc, 1u);
-          mma_tf32(tmem, smem_desc(al + o), smem_desc(bh + o), idesc, 1u);
+          const uint32_t acc = (first && ks == 0) ? 0u : 1u;
+          mma_tf32(dt, smem_desc(ah + o), smem_desc(bh + o), idesc, acc);
+          mma_tf32(dt, smem_desc(ah + o), smem_desc(bl + o), idesc, 1u);
+          mma_tf32(dt, smem_desc(al + o), smem_desc(bh + o), idesc, 1u);
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      ::"r"(smem_u32(&mmab[buf])) : "memory");
@@ -206,32 +286,37 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
       const int64_t last = issued - 1;
       if (!mbar_wait(&mmab[last & 1], (uint32_t)(last >> 1) & 1u)) *s_fail = 1;
     }
+    asm volatile("bar.sync 1, %0;" ::"r"(kTcConsumers) : "memory");
+    // the last one or two runs (consecutive: distinct regions)
+    if (!*reinterpret_cast<volatile int*>(s_fail))
+      for (int64_t g = drained; g < (issued + Sh::GROUP - 1) / Sh::GROUP; ++g) drain(g);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  // ---------------- epilogue: accumulator -> FP64 [3m][6m] in shared memory ----------------
+  // ---------------- epilogue: compensated sums -> FP64 [3m][6m] in shared memory ----------------
   double* E = reinterpret_cast<double*>(bufs);
-  if (warp < 4) {
-    const int row = warp * 32 + lane;
-    for (int c0 = 0; c0 < Sh::NB; c0 += 16) {
-      uint32_t r[16];
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                     "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                   : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < Sh::NS) {
+  auto sum_of = [](const float (&sv)[Sh::H0], const float (&cv)[Sh::NC], int j) -> double {
+    if constexpr (Sh::KAHAN) return (double)sv[j] - (double)cv[j];
+    else return (double)sv[j];
+  };
+  if (drainer) {
+    const int row = quarter * 32 + lane;
+    const bool ok = my_tiles > 0 && !*s_fail && !*p_fail;
+    if (row < Sh::NS) {
+      if (half == 0) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (c0 + j < Sh::NB) E[row * Sh::NB + c0 + j] = (my_tiles > 0 && !*s_fail && !*p_fail) ? (double)__uint_as_float(r[j]) : 0.0;
+        for (int j = 0; j < Sh::H0; ++j) E[row * Sh::NB + j] = ok ? sum_of(ks_s, ks_c, j) : 0.0;
+      } else {
+#pragma unroll
+        for (int j = 0; j < Sh::H1; ++j) E[row * Sh::NB + Sh::H0 + j] = ok ? sum_of(ks_s, ks_c, j) : 0.0;
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Sh::TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Sh::TMEM_ALLOC) : "memory");
   if ((*s_fail || *p_fail) && a.st && threadIdx.x == 0) {
     a.st->err = MGE_ETIMEOUT; a.st->bad_stage = 8; a.st->done = DONE_ERROR;
   }

@@ -851,7 +851,7 @@ mge_status build_phase1(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* rp_
       qop.shift = 0.0; qop.b = nullptr;
       qop.dinv = (o.precision == MGE_FP64) ? (const void*)ops->dinv_q.p : (const void*)ops->dinv_q32.p;
       qop.norm = ops->norm_q; qop.bmax = 1.0; qop.deflate = true; qop.beta = ops->beta_q;
-      qop.precond_degree = o.eps_precond_degree > 0 ? std::min(o.eps_precond_degree, 64) : default_eps_precond_degree(n);
+      qop.precond_degree = o.eps_precond_degree > 0 ? std::min(o.eps_precond_degree, kMaxPrecondDegree) : default_eps_precond_degree(n);
       qop.nnz = ops->nnz_q;
       qop.rr_fp64 = o.precision == MGE_FP64;
       qop.pc_bf16 = o.precision == MGE_BF16;

@@ -991,6 +991,7 @@ struct Solver {
   double tol;
   int maxiter;
   bool inverse_rr = true;
+  bool rr_auto = false;             // inverse form first, FP64 Jacobi once the residuals stall
   double tau = 1e-12, tau_p = 1e-16, tau_w = 1e-10;
   int64_t nnz_a = 0, nnz_pc = 0;
 
@@ -1010,7 +1011,7 @@ struct Solver {
     MGE_TRY(W.scratch(ctx, blk, st)); MGE_TRY(AW.scratch(ctx, blk, st));
     MGE_TRY(Wr.scratch(ctx, blk, st));
     wsrc = Wr.p;
-    cheb_deg = std::max(1, std::min(op.precond_degree, 64));
+    cheb_deg = std::max(1, std::min(op.precond_degree, kMaxPrecondDegree));
     pc_bf16 = sizeof(T) == 4 && op.pc_bf16 && cheb_deg > 1 && op.sl_slp != nullptr;
     if (pc_bf16) {
       MGE_TRY(WrB.scratch(ctx, blk, st)); MGE_TRY(Yb0.scratch(ctx, blk, st));
@@ -1047,6 +1048,7 @@ struct Solver {
     // the inverse-pencil Rayleigh-Ritz needs G_A positive definite: A = L - mu Q + eps I with
     // eps > 0, or Q with the constant vector deflated
     inverse_rr = (sizeof(T) == 4) && !op.rr_fp64 && (op.shift > 0.0 || op.deflate);
+    rr_auto = inverse_rr && op.rr_switch;
     return MGE_OK;
   }
 
@@ -1162,8 +1164,14 @@ struct Solver {
     RRArgs r{};
     r.sm = sm; r.smt = smt; r.is_double = sizeof(T) == 8; r.ncl = gram_ncl;
     r.M = M; r.nb = nb; r.nx = nx; r.tau = tau; r.tau_p = tau_p; r.st = state;
+    r.sel = rr_auto ? RR_FP32 : RR_ALWAYS;
     launch_rr(st, r, inverse_rr);
     MGE_LAUNCHED(ctx, 1);
+    if (rr_auto) {
+      r.sel = RR_FP64;
+      launch_rr(st, r, false);
+      MGE_LAUNCHED(ctx, 1);
+    }
   }
 
   void launch_update(int nb, bool init, bool produce_p) {
@@ -1302,8 +1310,18 @@ struct Solver {
     w.M = M; w.K = K; w.has_x = hx; w.has_p = hp; w.check = check;
     w.deflate = op.deflate; w.n = n; w.tol = tol; w.norm = op.norm; w.bmax = op.bmax;
     w.tau_w = tau_w; w.maxiter = maxiter; w.st = state;
-    launch_wprep(st, w, sizeof(T) == 8 || op.rr_fp64);
-    MGE_LAUNCHED(ctx, 1);
+    if (rr_auto) {
+      // the FP64 launch first: a switch made by the FP32 launch takes effect next iteration
+      w.sel = RR_FP64; w.rr_switch = 0;
+      launch_wprep(st, w, true);
+      w.sel = RR_FP32; w.rr_switch = 1;
+      launch_wprep(st, w, false);
+      MGE_LAUNCHED(ctx, 2);
+    } else {
+      w.sel = RR_ALWAYS; w.rr_switch = 0;
+      launch_wprep(st, w, sizeof(T) == 8 || op.rr_fp64);
+      MGE_LAUNCHED(ctx, 1);
+    }
   }
 
   void launch_gram_w(bool hx, bool hp) {
@@ -1459,6 +1477,7 @@ struct Solver {
     }
     res->iters = hst->iter;
     res->drops = hst->drops;
+    res->rr64_from = op.rr_fp64 || sizeof(T) == 8 || !inverse_rr ? 0 : hst->rr64 ? hst->rr64_iter : -1;
     res->lambda.assign(hst->lambda, hst->lambda + K);
     res->eta.assign(hst->eta, hst->eta + K);
     if (V_out && (*status == MGE_OK || *status == MGE_ENOTCONVERGED)) {
@@ -1543,7 +1562,7 @@ struct Solver {
       MGE_CUDA(ctx, cudaGraphInstantiate(&gexec, graph, 0));
       if (timed) { cap_bytes = ctx->ev_bytes; ctx->ev_used = 0; ctx->ev_bytes.clear(); }
     }
-    const uint64_t per_chunk = (uint64_t)check_every * (6 + (cheb_deg - 1));
+    const uint64_t per_chunk = (uint64_t)check_every * (6 + (cheb_deg - 1) + (rr_auto ? 2 : 0));
     for (;;) {
       MGE_CUDA(ctx, cudaMemcpyAsync(hst, state, sizeof(State), cudaMemcpyDeviceToHost, st));
       MGE_CUDA(ctx, cudaStreamSynchronize(st));

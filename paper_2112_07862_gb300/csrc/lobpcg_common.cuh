@@ -27,6 +27,10 @@ struct State {
   int kept;
   int bad_stage;     // 1: Rayleigh-Ritz input, 2: residual / Ritz values, 3: W Gram, 4: RR output
   int loops;         // passes of the device-side iteration loop (graph mode)
+  int rr64;          // FP32 blocks: Rayleigh-Ritz and W's Cholesky now run in FP64
+  int rr64_iter;     // iteration after which they switched (0: from the start)
+  int best_iter;     // last iteration that halved the largest relative residual
+  float best_rho;    // that residual
   int pad1;
   long long rr_clk[16];     // clock64 deltas at the phase boundaries of the last Rayleigh-Ritz
   long long wp_clk[8];      // and of the last wprep (diagnostics)
@@ -218,8 +222,22 @@ struct RRArgs {
   int M, nb, nx;        // basis: nb blocks of M columns, the first nx of which are X
   double tau;           // dependence threshold (pivot^2 of a unit-diagonal Gram)
   double tau_p;         // threshold for dropping an empty P direction
+  int sel;              // RR_ALWAYS, or RR_FP32 / RR_FP64: run only in that phase of a solve
   State* st;
 };
+
+// Rayleigh-Ritz precision of an FP32 solve that may switch (State::rr64): both forms are
+// launched each iteration and the one not selected returns at once.
+enum : int { RR_ALWAYS = 0, RR_FP32 = 1, RR_FP64 = 2 };
+// An FP32 solve moves to the FP64 Rayleigh-Ritz once the largest relative residual of the
+// wanted pairs, below kRRStallGate times the tolerance, has not halved for kRRStallIters
+// iterations.  (The first iterations of a preconditioned solve can go that long without
+// halving it; measured on a 2M-node sphere: 9.4 after 10 iterations, 0.36 after 20.)
+constexpr int kRRStallIters = 10;
+constexpr float kRRStallGate = 1000.f;
+__device__ __forceinline__ bool rr_selected(int sel, const State* st) {
+  return sel == RR_ALWAYS || (sel == RR_FP64) == (st->rr64 != 0);
+}
 
 struct WprepArgs {
   Small* sm;
@@ -234,6 +252,8 @@ struct WprepArgs {
   int64_t n;
   double tol, norm, bmax, tau_w;
   int maxiter;
+  int sel;              // as RRArgs::sel
+  int rr_switch;        // this launch may move the solve to the FP64 Rayleigh-Ritz
   State* st;
 };
 

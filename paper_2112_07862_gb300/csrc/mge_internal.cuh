@@ -262,6 +262,7 @@ mge_status betweenness_run(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* 
 // 21 iterations and 162 / 95 / 65 / 49 / 45 ms at degree 16 / 24 / 32 / 48 / 64; the eps
 // solve converges in about 23 iterations at 24)
 constexpr int kDefaultPrecondDegree = 64;
+constexpr int kMaxPrecondDegree = 256;      // largest degree a caller may ask for
 constexpr int kDefaultEpsPrecondDegree = 24;
 // Defaults by graph size.  The best degree grows with n (the spectrum to flatten widens as the
 // smallest eigenvalues shrink): measured best embedding degree 24 on graphs of 2k-50k nodes
@@ -297,6 +298,7 @@ struct LobOp {
   double beta = 2;                 // upper bound of the spectrum of diag(A)^-1 A
   int precond_degree = 1;          // Chebyshev preconditioner degree (1: Jacobi)
   bool rr_fp64 = false;            // FP32 blocks: Rayleigh-Ritz and W's Cholesky in FP64
+  bool rr_switch = true;           // FP32 blocks: move to FP64 for both when the residuals stall
   bool pc_bf16 = false;            // FP32 blocks: the preconditioner's blocks in BF16
   bool gram_cuda_cores = false;    // FP32 blocks: Rayleigh-Ritz Grams on the CUDA cores only
   // operator the preconditioner applies, in the same difference form (pc_ptr NULL: the
@@ -359,6 +361,7 @@ struct LobResult {
   mge_status status = MGE_OK;
   int iters = 0;
   int drops = 0;
+  int rr64_from = -1;              // FP64 Rayleigh-Ritz: -1 never, 0 from the start, k after iteration k
   std::vector<double> lambda;      // [K]
   std::vector<double> eta;         // [K]
   double ms = 0;

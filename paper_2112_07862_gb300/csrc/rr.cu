@@ -156,7 +156,7 @@ __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int 
 constexpr int kRRThreads = 512;
 
 __global__ void __launch_bounds__(kRRThreads) k_rr_inv(RRArgs a) {
-  if (a.st->done) return;
+  if (a.st->done || !rr_selected(a.sel, a.st)) return;
   long long clk0 = clock64();
 #define RR_MARK(k) do { __syncthreads(); if (threadIdx.x == 0) a.st->rr_clk[k] = clock64() - clk0; } while (0)
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -616,7 +616,7 @@ __device__ __forceinline__ float warp_sum4(float s0, float s1, float s2, float s
 }
 
 __global__ void __launch_bounds__(kRWThreads) k_rr_warp(RRArgs a) {
-  if (a.st->done) return;
+  if (a.st->done || !rr_selected(a.sel, a.st)) return;
   const long long clk0 = clock64();
   __shared__ long long sclk[12];
   // phase clocks: written by every thread (a branch around clock64 leaves warps diverged)
@@ -1201,7 +1201,7 @@ __device__ int jacobi_eig(double* A, double* V, int ld, int k) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_rr_jacobi(RRArgs a) {
-  if (a.st->done) return;
+  if (a.st->done || !rr_selected(a.sel, a.st)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = a.M, n = a.nb * a.M, nx = a.nx;
   const int ld = n + 1;
@@ -1411,7 +1411,7 @@ __device__ void chol_drop_warp(R* S, int ld, int n, const R* tau, int* keep, R* 
 // ---------------------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_wprep(WprepArgs a) {
-  if (a.st->done) return;
+  if (a.st->done || !rr_selected(a.sel, a.st)) return;
   const int M = a.M;
   Small* sm = a.sm;
   // The FP64 Gram partials are rounded to R once; everything after runs in R (FP32 for FP32
@@ -1438,6 +1438,9 @@ __global__ void __launch_bounds__(kThreads) k_wprep(WprepArgs a) {
     cs[t] = (R)v;
   }
   int bad = 0, unconv = 0;
+  __shared__ int rmax_bits;     // largest relative residual of the wanted pairs (float bits)
+  if (threadIdx.x == 0) rmax_bits = 0;
+  __syncthreads();
   if (a.check) {
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
       const double rn2 = a.ncl_n == 1 ? sm->partN[0][k] : sum_strided(&sm->partN[0][k], a.ncl_n, 2 * MAXM);
@@ -1454,6 +1457,7 @@ __global__ void __launch_bounds__(kThreads) k_wprep(WprepArgs a) {
       a.st->eta[k] = (double)eta;
       a.st->lambda[k] = lam;
       unconv |= k < a.K && !(eta <= (float)a.tol);
+      if (k < a.K && isfinite(eta)) atomicMax(&rmax_bits, __float_as_int(eta));   // eta >= 0
     }
   }
   bad = __syncthreads_or(bad);
@@ -1464,6 +1468,15 @@ __global__ void __launch_bounds__(kThreads) k_wprep(WprepArgs a) {
     if (bad) { a.st->done = DONE_ERROR; a.st->err = MGE_ENOTFINITE; a.st->bad_stage = 2; }
     else if (!unconv) a.st->done = DONE_CONVERGED;
     else if (a.st->iter >= a.maxiter) a.st->done = DONE_MAXITER;
+    // stagnation of an FP32 Rayleigh-Ritz: its eigenvectors carry errors of about u times the
+    // spread of the pencil, which floor the relative residual (measured: ~1e-5 on a 2M-node
+    // sphere, whose eigenvalues come in near-degenerate groups); the FP64 form continues
+    if (a.rr_switch && !a.st->done && !a.st->rr64) {
+      const float r = __int_as_float(rmax_bits);
+      if (!(r <= kRRStallGate * (float)a.tol)) a.st->best_iter = 0;     // not near the target yet
+      else if (a.st->best_iter == 0 || r <= 0.5f * a.st->best_rho) { a.st->best_rho = r; a.st->best_iter = a.st->iter; }
+      else if (a.st->iter - a.st->best_iter >= kRRStallIters) { a.st->rr64 = 1; a.st->rr64_iter = a.st->iter; }
+    }
   }
   const int ox = 0, op = a.has_x ? M : 0, ow = (a.has_x ? M : 0) + (a.has_p ? M : 0);
   const R inv_n = (R)(1.0 / (double)a.n);

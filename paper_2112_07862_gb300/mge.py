@@ -59,7 +59,7 @@ class mge_embed_opts(C.Structure):
 
 class mge_embed_info(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("m", C.c_int), ("drops", C.c_int),
-                ("resid", C.c_double * 64), ("solve_ms", C.c_double)]
+                ("resid", C.c_double * 64), ("solve_ms", C.c_double), ("rr_fp64_from", C.c_int)]
 
 
 class mge_request(C.Structure):
@@ -468,7 +468,8 @@ def embed_opts(precision="fp32", guard=0, maxiter=0, seed=0, check_every=0, use_
     o.v_on_device = 1 if v_on_device else 0
     o.stream = stream
     o.precond_degree = precond_degree
-    o.rr_fp64 = 1 if rr_fp64 else 0
+    # True / 1: FP64 throughout; False / 0: automatic; -1: FP32 throughout
+    o.rr_fp64 = int(rr_fp64)
     o.gram_cuda_cores = 1 if gram_cuda_cores else 0
     return o
 
