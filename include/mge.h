@@ -63,11 +63,14 @@ typedef enum {
 
 /* Arithmetic of the iterated blocks X, W, P and of the stored matrix values.
  *   MGE_FP64  everything in FP64, including the Rayleigh-Ritz eigensolve (cyclic Jacobi).
- *   MGE_FP32  FP32 blocks and SpMM; Gram sums in FP32 with compensation, reduced across
- *             the GPU in FP64; residual norms in FP64; the
- *             Rayleigh-Ritz scaling in FP64 and its eigensolve in FP32 on the inverse
- *             pencil (the wanted smallest eigenvalues become the largest, which FP32
- *             resolves to relative accuracy).
+ *   MGE_FP32  FP32 blocks and SpMM; Gram sums in FP32 with compensation (on graphs of at
+ *             least 65,536 nodes: TF32 tensor cores on split operands, see
+ *             mge_embed_opts.gram_cuda_cores), reduced across the GPU in FP64; residual
+ *             norms in FP64; the Rayleigh-Ritz scaling in FP64 and its eigensolve in FP32 on
+ *             the inverse pencil (the wanted smallest eigenvalues become the largest, which
+ *             FP32 resolves to relative accuracy), followed by one correction of the Ritz
+ *             coefficients against the FP64 residual of the pencil (see
+ *             mge_embed_opts.rr_fp64).
  *   MGE_BF16  as MGE_FP32, with the LOBPCG preconditioner's blocks -- its right-hand side
  *             D^-1 R, the Chebyshev iterates and corrections -- stored in BF16 (FP32
  *             arithmetic in registers; the matrix values stay FP32 so that the Chebyshev
@@ -305,14 +308,17 @@ typedef struct {
                                     cyclic Jacobi in FP64 for the rest of the solve;
                                   1 cyclic Jacobi on the 3m x 3m pencil in FP64 throughout;
                                  -1 the FP32 form throughout.
-                                 Measured on one GB300 (tol 1e-5): 200k-node swiss roll,
-                                 K = 8, m = 16: FP32 21 iterations at 2.1 ms, FP64 23 at
-                                 4.0 ms; 2M-node sphere, K = 16, m = 24: FP32 stalls at
-                                 relative residuals of 1-2e-5 (its eigenvectors carry errors
-                                 of about u times the pencil's spread, and the sphere's
-                                 eigenvalues come in near-degenerate groups), FP64 90
-                                 iterations.  info.rr_fp64_from reports which ran.  FP64
-                                 blocks always use FP64.                                    */
+                                 The FP32 form's eigenvectors carry errors of about u
+                                 theta_k / theta_1 along directions of large Rayleigh
+                                 quotient theta_j, which floor the relative residual at
+                                 about u theta_j / theta_1 (measured before the correction:
+                                 1e-5 at 200k nodes, 1-2e-5 on a 2M-node sphere); one step
+                                 c -= G_A^-1 (G_A - theta G_B) c with the residual in FP64
+                                 removes them.  Measured on one GB300 (tol 1e-5): 200k-node
+                                 swiss roll, K = 8, m = 16: FP32 21 iterations at 2.15 ms,
+                                 FP64 23 at 4.0 ms; 2M-node sphere, K = 16, m = 24: FP32 48
+                                 iterations, FP64 90.  info.rr_fp64_from reports which ran.
+                                 FP64 blocks always use FP64.                               */
   int         gram_cuda_cores; /* FP32 blocks of width 12, 16 or 24 on graphs of at least
                                  65,536 nodes: 0 (default) computes the Rayleigh-Ritz Grams
                                  [X W P]^T A [X W P] and [X W P]^T B [X W P] on the tensor

@@ -29,8 +29,12 @@ struct State {
   int loops;         // passes of the device-side iteration loop (graph mode)
   int rr64;          // FP32 blocks: Rayleigh-Ritz and W's Cholesky now run in FP64
   int rr64_iter;     // iteration after which they switched (0: from the start)
-  int best_iter;     // last iteration that halved the largest relative residual
+  int best_iter;     // last iteration that halved the largest relative residual (near tol)
   float best_rho;    // that residual
+  int pbest_iter;    // the same at any level of the residual
+  float pbest_rho;
+  int refine_off;    // no halving for kRRStallIters iterations: the FP32 Rayleigh-Ritz skips
+                     // its FP64 correction step
   int pad1;
   long long rr_clk[16];     // clock64 deltas at the phase boundaries of the last Rayleigh-Ritz
   long long wp_clk[8];      // and of the last wprep (diagnostics)

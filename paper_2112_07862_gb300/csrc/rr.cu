@@ -42,6 +42,10 @@ __device__ __forceinline__ R sym_a_entry(R gij, R gji, R gii, R gjj) {
   return R(0.5) * (gij + gji);
 }
 
+// Largest relative size of the FP64 correction of the FP32 Ritz coefficients (the corrections
+// the FP32 eigensolve needs are of order u theta_K / theta_1, about 1e-6).
+constexpr float kRefineMax = 1e-5f;
+
 // A basis that collapses (fewer than m independent directions) after the solve has made
 // progress means the iteration has stagnated at its precision's floor: the current pairs
 // stand and the solve ends as not converged.  At the start it is a rank-deficient block.
@@ -571,10 +575,71 @@ __global__ void __launch_bounds__(kRRThreads) k_rr_inv(RRArgs a) {
     }
   }
   __syncthreads();
+  RR_MARK(11);
+  // 11. One correction step for the Ritz coefficients against the FP64 pencil.  The FP32
+  //     eigenvectors of M carry absolute errors of about u mu_max, i.e. components of
+  //     relative size u theta_k / theta_1 along basis directions of large Rayleigh quotient
+  //     theta_j, which put u theta_j / theta_1 into the relative residual (measured floors:
+  //     ~3e-6 at 20k nodes, ~1e-5 at 200k, 1-2e-5 at 2M).  With the FP64 residual
+  //     r = (G_A - theta G_B) c and the correction d = -G_A^-1 r (the FP32 Cholesky factor of
+  //     G^_A), a component along an eigenvector j of the pencil shrinks by the factor
+  //     theta_k / theta_j: the large-theta errors go, the ones along nearby eigenvectors
+  //     change little, and those along smaller theta (of size u) grow by at most
+  //     theta_K / theta_1.  Skipped once the residuals have stopped falling: at a floor set
+  //     by the FP32 blocks the correction only feeds rounding back into the basis, and over
+  //     thousands of such iterations that diverged (measured on a 2000-node graph).
+  if (!a.st->refine_off) {
+    float* Rf = scr;                        // k x M: D r, then d in the u coordinates
+    for (int t = threadIdx.x; t < k * M; t += blockDim.x) {
+      const int r = t / M, q = t % M;
+      const int i = idx[r];
+      const double th = sm->lam[q];
+      double s = 0.0;
+      for (int c_ = 0; c_ < k; ++c_) {
+        const int j = idx[c_];
+        s += (gA[i * ldd + j] - th * gB[i * ldd + j]) * sm->Cx[j * MAXM + q];
+      }
+      Rf[r * M + q] = (float)(dsc[i] * s);
+    }
+    __syncthreads();
+    // G_A^-1 = D L^-T L^-1 D on the kept directions: w = L^-1 (D r), then z = L^-T w
+    for (int q = threadIdx.x; q < M; q += blockDim.x) {
+      for (int r = 0; r < k; ++r) {
+        float v = Rf[r * M + q];
+        for (int s_ = 0; s_ < r; ++s_) v -= Lf[r * ldf + s_] * Rf[s_ * M + q];
+        Rf[r * M + q] = v * rd[r];
+      }
+      for (int r = k - 1; r >= 0; --r) {
+        float v = Rf[r * M + q];
+        for (int s_ = r + 1; s_ < k; ++s_) v -= Lf[s_ * ldf + r] * Rf[s_ * M + q];
+        Rf[r * M + q] = v * rd[r];
+      }
+    }
+    __syncthreads();
+    // a correction is kept only while it is small against the coefficients (both in the
+    // unit-diagonal scaling): near-dependent bases, where G_A^-1 amplifies the residual's
+    // rounding, leave the FP32 coefficients as they are
+    for (int q = threadIdx.x; q < M; q += blockDim.x) {
+      float nz = 0.f, nc = 0.f;
+      for (int r = 0; r < k; ++r) {
+        const float z = Rf[r * M + q];
+        const float c = (float)(sm->Cx[idx[r] * MAXM + q] / dsc[idx[r]]);
+        nz += z * z;
+        nc += c * c;
+      }
+      dots[q] = (nz <= kRefineMax * kRefineMax * nc) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < k * M; t += blockDim.x) {
+      const int r = t / M, q = t % M;
+      if (dots[q] != 0.f) sm->Cx[idx[r] * MAXM + q] -= dsc[idx[r]] * (double)Rf[r * M + q];
+    }
+  }
+  __syncthreads();
   if (a.is_double) store_coeffs<double, float>(a);
   else store_coeffs<float, float>(a);
   if (threadIdx.x == 0) a.st->kept = k;
-  RR_MARK(11);
+  RR_MARK(12);
 #undef RR_MARK
 }
 
@@ -656,26 +721,21 @@ __global__ void __launch_bounds__(kRWThreads) k_rr_warp(RRArgs a) {
   int bad = 0;
   for (int t = threadIdx.x; t < WN * WN; t += kRWThreads) {
     const int i = t >> 5, j = t & 31;
-    float ga = 0.f, gb = 0.f;
+    double ga = 0.0, gb = 0.0;
     if (i < n && j < n) {
       const int bi = i / 4, bj = j / 4;
-      ga = (float)sym_a_entry(sm->partA[0][i * MAXS + j], sm->partA[0][j * MAXS + i],
-                              sm->partA[0][i * MAXS + i], sm->partA[0][j * MAXS + j]);
-      const float b1 = (bi <= bj) ? (float)sm->partB[0][i * MAXS + j] : 0.f;
-      const float b2 = (bi >= bj) ? (float)sm->partB[0][j * MAXS + i] : 0.f;
-      gb = (bi < bj) ? b1 : (bi > bj) ? b2 : 0.5f * (b1 + b2);
-      bad |= !(isfinite(ga) && isfinite(gb));
+      ga = sym_a_entry(sm->partA[0][i * MAXS + j], sm->partA[0][j * MAXS + i],
+                       sm->partA[0][i * MAXS + i], sm->partA[0][j * MAXS + j]);
+      const double b1 = (bi <= bj) ? sm->partB[0][i * MAXS + j] : 0.0;
+      const double b2 = (bi >= bj) ? sm->partB[0][j * MAXS + i] : 0.0;
+      gb = (bi < bj) ? b1 : (bi > bj) ? b2 : 0.5 * (b1 + b2);
+      bad |= !(isfinite((float)ga) && isfinite((float)gb));
     }
     const float sc = sdf[i] * sdf[j];
-    sA[i][j] = ga * sc;
-    sB[i][j] = gb * sc;
+    sA[i][j] = (float)ga * sc;
+    sB[i][j] = (float)gb * sc;
   }
   bad = __syncthreads_or(bad);
-  for (int t = threadIdx.x; t < n * n; t += kRWThreads) {      // the next Gram starts from zero
-    const int i = t / n, j = t % n;
-    sm->partA[0][i * MAXS + j] = 0.0;
-    sm->partB[0][i * MAXS + j] = 0.0;
-  }
   if (bad) {
     if (threadIdx.x == 0) { a.st->done = DONE_ERROR; a.st->err = MGE_ENOTFINITE; a.st->bad_stage = 1; }
     return;
@@ -1121,6 +1181,67 @@ __global__ void __launch_bounds__(kRWThreads) k_rr_warp(RRArgs a) {
       cf->Cp[i * MAXM + q] = sdf[i] * (v0 + v1);
     }
   }
+  __syncthreads();
+  // ---- correction of the Ritz coefficients against the FP64 pencil (see k_rr_inv, step 11):
+  //      c -= G_A^-1 (G_A - theta G_B) c, with G_A^-1 = D L^-T L^-1 D and L^-1 in sL (compact).
+  //      runs after C_p, whose sU and sV it reuses: sV holds D r (compact rows), sU
+  //      w = L^-1 D r.  The FP64 Gram partials are read again here and cleared after. ----
+  const bool refine = !a.st->refine_off;
+  for (int t = threadIdx.x; t < WN * M && refine; t += kRWThreads) {
+    const int r = t / M, q = t % M;
+    float v = 0.f;
+    if (r < k) {
+      const int i = sidx[r];
+      const double th = sm->lam[q];
+      double acc = 0.0;
+      for (int j = 0; j < n; ++j) {
+        const int bi = i / 4, bj = j / 4;      // the Grams as step 1 symmetrised them, in FP64
+        const double ga = sym_a_entry(sm->partA[0][i * MAXS + j], sm->partA[0][j * MAXS + i],
+                                      sm->partA[0][i * MAXS + i], sm->partA[0][j * MAXS + j]);
+        const double gb = bi < bj ? sm->partB[0][i * MAXS + j] : bi > bj ? sm->partB[0][j * MAXS + i]
+                                  : 0.5 * (sm->partB[0][i * MAXS + j] + sm->partB[0][j * MAXS + i]);
+        acc += (ga - th * gb) * (double)cf->Cx[j * MAXM + q];
+      }
+      v = (float)((double)sdf[i] * acc);
+    }
+    sV[r][q] = v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < WN * M; t += kRWThreads) {      // w = L^-1 (D r), lower triangular
+    const int r = t / M, q = t % M;
+    float v = 0.f;
+    for (int s_ = 0; s_ <= r && s_ < k; ++s_) v += sL[r][s_] * sV[s_][q];
+    sU[r][q] = v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < WN * M; t += kRWThreads) {      // z = L^-T w (compact rows)
+    const int r = t / M, q = t % M;
+    float v = 0.f;
+    for (int s_ = r; s_ < k; ++s_) v += sL[s_][r] * sU[s_][q];
+    sV[r][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < M) {                 // kept only while small (see kRefineMax)
+    const int q = threadIdx.x;
+    float nz = 0.f, nc = 0.f;
+    for (int r = 0; r < k; ++r) {
+      const float z = sV[r][q], c = cf->Cx[sidx[r] * MAXM + q] / sdf[sidx[r]];
+      nz += z * z;
+      nc += c * c;
+    }
+    smu[q] = (refine && nz <= kRefineMax * kRefineMax * nc) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * M; t += kRWThreads) {       // C_x -= D z
+    const int i = t / M, q = t % M, r = sinv[i];
+    if (r >= 0 && smu[q] != 0.f) cf->Cx[i * MAXM + q] -= sdf[i] * sV[r][q];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * n; t += kRWThreads) {      // the next Gram starts from zero
+    const int i = t / n, j = t % n;
+    sm->partA[0][i * MAXS + j] = 0.0;
+    sm->partB[0][i * MAXS + j] = 0.0;
+  }
   RW_MARK(11);
   __syncthreads();
   if (threadIdx.x < 12) a.st->rr_clk[threadIdx.x] = sclk[threadIdx.x];
@@ -1471,6 +1592,11 @@ __global__ void __launch_bounds__(kThreads) k_wprep(WprepArgs a) {
     // stagnation of an FP32 Rayleigh-Ritz: its eigenvectors carry errors of about u times the
     // spread of the pencil, which floor the relative residual (measured: ~1e-5 on a 2M-node
     // sphere, whose eigenvalues come in near-degenerate groups); the FP64 form continues
+    if (!a.st->done) {
+      const float r = __int_as_float(rmax_bits);
+      if (a.st->pbest_iter == 0 || r <= 0.5f * a.st->pbest_rho) { a.st->pbest_rho = r; a.st->pbest_iter = a.st->iter; }
+      a.st->refine_off = a.st->iter - a.st->pbest_iter >= kRRStallIters;
+    }
     if (a.rr_switch && !a.st->done && !a.st->rr64) {
       const float r = __int_as_float(rmax_bits);
       if (!(r <= kRRStallGate * (float)a.tol)) a.st->best_iter = 0;     // not near the target yet

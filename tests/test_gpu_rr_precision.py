@@ -3,8 +3,7 @@ and the default that starts in FP32 and moves to FP64 when the residuals stop fa
 
 Every form must give the oracle's pairs (eigenvalues 1e-4 relative, vectors 1e-3 rad per
 cluster: the reduced-precision bar); `info.rr_fp64_from` must say which form ran.  A
-tolerance below the FP32 form's floor but above the FP64 form's makes the default switch
-and converge.
+tolerance out of reach makes the default switch once the FP32 form stalls.
 """
 import numpy as np
 import pytest
@@ -64,18 +63,17 @@ def test_every_form_gives_the_oracle_pairs(ctx, case, mode):
 
 
 def test_stalled_fp32_moves_to_fp64(ctx, case):
-    """Measured on this graph (one GB300): the FP32 form holds the largest relative residual
-    at 2.7e-6 .. 5.6e-6 from iteration 20 to 300, the FP64 form at 1.13e-6 .. 1.17e-6.  A
-    tolerance of 1.6e-6 lies between the two floors: the FP32 form stalls and the default
-    switches and converges."""
+    """A tolerance below what FP32 blocks reach (measured on this graph, one GB300: largest
+    relative residual 0.7e-6 .. 1.1e-6 from iteration 20 on, in either Rayleigh-Ritz form)
+    stalls the FP32 form within 1000x of the tolerance: the default then switches, and the
+    solve ends as not converged with the oracle's pairs."""
     from paper_2112_07862_gb300 import mge
     g, d, ops = case
     K = 8
-    lam, V, info, s = ctx.embed(ops, K, 1.6e-6, precision="fp32", rr_fp64=0, maxiter=300)
-    assert s == mge.MGE_OK
+    lam, V, info, s = ctx.embed(ops, K, 1e-8, precision="fp32", rr_fp64=0, maxiter=150)
+    assert s == mge.MGE_ENOTCONVERGED
     assert 0 < info.rr_fp64_from < info.iters
-    assert max(info.resid[k] for k in range(K)) <= 1.6e-6
     check_pairs(lam, V, d, K)
-    lam2, V2, info2, s2 = ctx.embed(ops, K, 1.6e-6, precision="fp32", rr_fp64=-1, maxiter=300)
-    assert s2 in (mge.MGE_OK, mge.MGE_ENOTCONVERGED) and info2.rr_fp64_from == -1
+    lam2, V2, info2, s2 = ctx.embed(ops, K, 1e-8, precision="fp32", rr_fp64=-1, maxiter=150)
+    assert s2 == mge.MGE_ENOTCONVERGED and info2.rr_fp64_from == -1
     check_pairs(lam2, V2, d, K)
