@@ -15,7 +15,7 @@
 // residual just under a 1e-5 tolerance.  The CTAs' sums are reduced in FP64.
 //
 // Per CTA: a producer warp streams each tile's six 32 x m block slices and the 32 b_i into a
-// ring of three shared-memory stages with 1-D bulk copies (TMA); eight consumer warps split
+// ring of shared-memory stages (7, or 4 at m = 24) with 1-D bulk copies (TMA); eight consumer warps split
 // the values and write both operands in the K-major, non-swizzled layout of the tensor cores
 // (8-row x 16-byte core matrices: element (row r, k) at (r/8)*1024 + (k/4)*128 + (r%8)*16 +
 // (k%4)*4), into one of two operand buffers; one thread issues the twelve MMAs of the tile and
@@ -36,7 +36,6 @@ constexpr int kTcThreads = kTcConsumers + 32;     // plus the producer warp
 constexpr int kTcT = 32;                          // rows per tile (the MMAs' K)
 constexpr int kLBO = 128;                         // bytes between K-adjacent core matrices
 constexpr int kSBO = (kTcT / 4) * 128;            // bytes between 8-row groups
-constexpr int kNRaw = 3;
 constexpr int kTcCluster = 8;                     // CTAs per cluster (DSMEM reduction)
 
 template <int M>
@@ -49,18 +48,21 @@ struct TcShape {
   static constexpr int B_BYTES = NMMA * kTcT * 4;
   static constexpr int BUF = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int HDR = 1024;
-  static constexpr int SMEM = HDR + kNRaw * RAW + 2 * BUF;
+  // raw stages in flight: as many as shared memory allows, up to 7 (the tile loads are the
+  // kernel's critical path: ~40 KB in flight per SM with 3 stages left it waiting on them)
+  static constexpr int NRAW = M == 24 ? 4 : 7;
+  static constexpr int SMEM = HDR + NRAW * RAW + 2 * BUF;
+  static_assert(SMEM <= 227 * 1024, "shared memory");
   static constexpr int TMEM_COLS = NMMA <= 32 ? 32 : NMMA <= 64 ? 64 : NMMA <= 128 ? 128 : 256;
   static constexpr int TMEM_ALLOC = 2 * TMEM_COLS;                // two accumulator regions
   static constexpr int H0 = (NB / 2 + 7) / 8 * 8;                 // columns of half 0 (x8 loads)
   static constexpr int H1 = NB - H0;
   static constexpr int QUARTERS = (NS + 31) / 32;                 // lane quarters holding rows
   // Register sums: compensated (Kahan) where two floats per column fit the 168 registers a
-  // thread gets at 288 threads per CTA (m <= 16), plain FP32 at m = 24.  Run length: the error
-  // of the sums grows about as sqrt(runs) (plain) while that of a run grows with its length,
-  // so the plain sums take longer runs.
+  // thread gets at 288 threads per CTA (m <= 16), plain FP32 at m = 24.  Runs of 8 tiles: the
+  // error of a run grows with its length, that of plain register sums as sqrt(runs).
   static constexpr bool KAHAN = M <= 16;
-  static constexpr int GROUP = KAHAN ? 4 : 8;                    // tiles per accumulation run
+  static constexpr int GROUP = 8;                                // tiles per accumulation run
   static constexpr int NC = KAHAN ? H0 : 1;                      // compensation terms
   static_assert(GROUP >= 2, "a region is drained two tiles after its run ends");
   static_assert(NS <= 128 && NMMA <= 256, "Gram shape exceeds one MMA");
@@ -86,10 +88,12 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, 
                ::"r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
 }
 
+// x rounded to the 10-bit TF32 mantissa, to nearest with ties away from zero: add half a unit
+// of the 13th bit to the magnitude's bit pattern (a carry moves into the exponent as it
+// should) and clear the 13 low bits.  Integer operations: the conversion instruction runs
+// at a fraction of the FP32 rate, and every Gram tile converts ~9,000 values.
 __device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
@@ -131,20 +135,21 @@ template <int M>
 __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
   using Sh = TcShape<M>;
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem);            // [kNRaw]
-  uint64_t* empty = full + 4;                                    // [kNRaw]
-  uint64_t* mmab = full + 8;                                     // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 128);
+  static_assert(Sh::NRAW <= 8, "header layout");
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);            // [NRAW]
+  uint64_t* empty = full + 8;                                    // [NRAW]
+  uint64_t* mmab = full + 16;                                    // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 160);
   int* s_fail = reinterpret_cast<int*>(smem + 192);      // a consumer wait gave up
   int* s_done = reinterpret_cast<int*>(smem + 196);
   int* p_fail = reinterpret_cast<int*>(smem + 200);      // the producer's wait gave up
   unsigned char* raw = smem + Sh::HDR;
-  unsigned char* bufs = raw + kNRaw * Sh::RAW;
+  unsigned char* bufs = raw + Sh::NRAW * Sh::RAW;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   cg::cluster_group cl = cg::this_cluster();
 
   if (tid == 0) {
-    for (int s = 0; s < kNRaw; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], kTcConsumers); }
+    for (int s = 0; s < Sh::NRAW; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], kTcConsumers); }
     mbar_init(&mmab[0], 1);
     mbar_init(&mmab[1], 1);
     *s_fail = 0;
@@ -186,8 +191,8 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
     // ---------------- producer ----------------
     if (lane == 0) {
       for (int64_t i = 0; i < my_tiles; ++i) {
-        const int s = (int)(i % kNRaw);
-        if (i >= kNRaw && !mbar_wait(&empty[s], (uint32_t)((i / kNRaw) - 1) & 1u)) { *p_fail = 1; break; }
+        const int s = (int)(i % Sh::NRAW);
+        if (i >= Sh::NRAW && !mbar_wait(&empty[s], (uint32_t)((i / Sh::NRAW) - 1) & 1u)) { *p_fail = 1; break; }
         const int64_t r0 = (blockIdx.x + i * gridDim.x) * kTcT;
         const int nr = (int)(a.n - r0 < (int64_t)kTcT ? a.n - r0 : (int64_t)kTcT);
         const uint32_t blk = (uint32_t)nr * M * 4u;
@@ -209,10 +214,10 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
     int64_t issued = 0;                 // tiles whose MMAs were issued (the same in every consumer)
     int64_t drained = 0;                // runs drained (the same in every consumer)
     for (int64_t i = 0; i < my_tiles; ++i) {
-      const int s = (int)(i % kNRaw), buf = (int)(i & 1);
+      const int s = (int)(i % Sh::NRAW), buf = (int)(i & 1);
       const int64_t r0 = (blockIdx.x + i * gridDim.x) * kTcT;
       const int nr = (int)(a.n - r0 < (int64_t)kTcT ? a.n - r0 : (int64_t)kTcT);
-      bool ok = mbar_wait(&full[s], (uint32_t)(i / kNRaw) & 1u);
+      bool ok = mbar_wait(&full[s], (uint32_t)(i / Sh::NRAW) & 1u);
       if (ok && i >= 2) ok = mbar_wait(&mmab[buf], (uint32_t)((i - 2) >> 1) & 1u);
       if (!ok) *s_fail = 1;               // written before the barrier below, read after it
       const unsigned char* st = raw + (size_t)s * Sh::RAW;

@@ -33,8 +33,9 @@ struct State {
   float best_rho;    // that residual
   int pbest_iter;    // the same at any level of the residual
   float pbest_rho;
-  int refine_off;    // no halving for kRRStallIters iterations: the FP32 Rayleigh-Ritz skips
-                     // its FP64 correction step
+  int refine;        // the FP32 Rayleigh-Ritz applies its FP64 correction step: the largest
+                     // residual is within kRRStallGate of the tolerance and has halved in the
+                     // last kRRStallIters iterations
   int pad1;
   long long rr_clk[16];     // clock64 deltas at the phase boundaries of the last Rayleigh-Ritz
   long long wp_clk[8];      // and of the last wprep (diagnostics)

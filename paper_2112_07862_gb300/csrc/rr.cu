@@ -585,10 +585,11 @@ __global__ void __launch_bounds__(kRRThreads) k_rr_inv(RRArgs a) {
   //     G^_A), a component along an eigenvector j of the pencil shrinks by the factor
   //     theta_k / theta_j: the large-theta errors go, the ones along nearby eigenvectors
   //     change little, and those along smaller theta (of size u) grow by at most
-  //     theta_K / theta_1.  Skipped once the residuals have stopped falling: at a floor set
-  //     by the FP32 blocks the correction only feeds rounding back into the basis, and over
-  //     thousands of such iterations that diverged (measured on a 2000-node graph).
-  if (!a.st->refine_off) {
+  //     theta_K / theta_1.  Applied only near the tolerance (the floor matters there) and
+  //     not once the residuals have stopped falling: at a floor set by the FP32 blocks the
+  //     correction only feeds rounding back into the basis, and over thousands of such
+  //     iterations that diverged (measured on a 2000-node graph).
+  if (a.st->refine) {
     float* Rf = scr;                        // k x M: D r, then d in the u coordinates
     for (int t = threadIdx.x; t < k * M; t += blockDim.x) {
       const int r = t / M, q = t % M;
@@ -1186,7 +1187,7 @@ __global__ void __launch_bounds__(kRWThreads) k_rr_warp(RRArgs a) {
   //      c -= G_A^-1 (G_A - theta G_B) c, with G_A^-1 = D L^-T L^-1 D and L^-1 in sL (compact).
   //      runs after C_p, whose sU and sV it reuses: sV holds D r (compact rows), sU
   //      w = L^-1 D r.  The FP64 Gram partials are read again here and cleared after. ----
-  const bool refine = !a.st->refine_off;
+  const bool refine = a.st->refine != 0;
   for (int t = threadIdx.x; t < WN * M && refine; t += kRWThreads) {
     const int r = t / M, q = t % M;
     float v = 0.f;
@@ -1595,7 +1596,7 @@ __global__ void __launch_bounds__(kThreads) k_wprep(WprepArgs a) {
     if (!a.st->done) {
       const float r = __int_as_float(rmax_bits);
       if (a.st->pbest_iter == 0 || r <= 0.5f * a.st->pbest_rho) { a.st->pbest_rho = r; a.st->pbest_iter = a.st->iter; }
-      a.st->refine_off = a.st->iter - a.st->pbest_iter >= kRRStallIters;
+      a.st->refine = r <= kRRStallGate * (float)a.tol && a.st->iter - a.st->pbest_iter < kRRStallIters;
     }
     if (a.rr_switch && !a.st->done && !a.st->rr64) {
       const float r = __int_as_float(rmax_bits);
