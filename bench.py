@@ -33,8 +33,27 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "node-embeddings/s (K=8 generalized eigenvectors per node, relative residual <= 1e-5)"
 UNIT = "node-embeddings/s"
+
+
+def metric(a):
+    tol = ("%g" % a.tol).replace("e-0", "e-")
+    return f"node-embeddings/s (K={a.K} generalized eigenvectors per node, relative residual <= {tol})"
+
+
+def accuracy_note(a):
+    """Where the accuracy of this workload's results is checked."""
+    w = (a.shape, a.n, a.knn, a.K, a.seed)
+    if w == ("swiss_roll", 200_000, 10, 8, 2) and a.precision in ("fp32", "bf16"):
+        return ("eigenvalues within 1.2e-6 relative and eigenvectors within 1.4e-4 rad of the oracle's "
+                "machine-precision pairs on this workload (tests/test_gpu_fullsize.py)")
+    if w == ("sphere", 2_000_000, 10, 16, 3) and a.precision == "fp32":
+        return ("pairs checked by properties at this size (tests/test_gpu_sphere_2m.py): backward error <= 1e-6 "
+                "against the oracle's FP64 A and b, V^T B V = I, the sphere's 1-3-5-7 eigenvalue groups, eps "
+                "within the Courant-Fischer bracket")
+    if w[:2] == ("square", 1000) and a.precision == "fp64":
+        return "dense FP64 oracle parity on 1k-node graphs (tests/test_gpu_embed.py)"
+    return "not measured at this size"
 
 
 def parse():
@@ -308,7 +327,7 @@ def run_ours(a, dist):
                 "avg_launch_us": 1e3 * st.spmm_ms / st.spmm_launches if st.spmm_launches else None,
                 "algorithmic_bytes_per_launch": st.spmm_bytes / st.spmm_launches if st.spmm_launches else None}
     res = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": a.steps,
+        "metric": metric(a), "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if a.precision == "fp32" else a.precision.replace("fp", "f"),
         "data": f"synthetic: seeded {a.shape.replace('_', '-')} points, exact symmetric kNN graph, Gaussian weights",
@@ -322,8 +341,7 @@ def run_ours(a, dist):
                    "embed_ms": statistics.mean(phases["embed_ms"][:a.steps]),
                    "eps_iters": statistics.mean(phases["eps_iters"][:a.steps])},
         "status": {"build": status["build"], "embed": status["embed"]},
-        "accuracy_note": "eigenvalues within 1e-6 relative and eigenvectors within 1.4e-4 rad of the oracle's "
-                         "machine-precision pairs on this workload (tests/test_gpu_fullsize.py)",
+        "accuracy_note": accuracy_note(a),
         "roofline": roofline,
         "e2e": e2e,
         "clocks": clk,
@@ -624,7 +642,7 @@ def run_reference(a, dist):
         oracle_step(a, n, a.seed)
     t, c = time.perf_counter() - t0, time.process_time() - c0
     v = n * a.steps / t
-    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": dist.world,
+    return {"impl": "reference", "metric": metric(a), "value": v, "unit": UNIT, "n_gpus": dist.world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(workload(a), sample=f"N={n} per step (bounded sample of the workload)"),
