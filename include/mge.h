@@ -107,6 +107,7 @@ typedef struct {
   double   spmm_ms;           /* their summed CUDA-event duration                           */
   uint64_t spmm_bytes;        /* their summed algorithmic bytes                             */
   size_t   hbm_in_use;        /* bytes of device memory the context holds                   */
+  uint64_t tune_entries;      /* kernel configurations the context's autotuner holds        */
 } mge_stats;
 
 /* Copies the context's counters.  mge_ctx_set_timing(ctx, 1) brackets every SpMM launch
@@ -114,6 +115,23 @@ typedef struct {
 mge_status mge_ctx_stats(const mge_ctx* ctx, mge_stats* out);
 mge_status mge_ctx_set_timing(mge_ctx* ctx, int on);
 mge_status mge_ctx_reset_stats(mge_ctx* ctx);
+
+/* Kernel autotuning.  The LOBPCG preconditioner's Chebyshev step (the solve's dominant kernel)
+ * has several launch configurations -- its shared-memory stage budget (32, 48, 64 or 96 KB per
+ * CTA: staged indices against L1 room for the gathers in flight) and, in FP32, whether each
+ * row's own blocks are loaded before its gathers -- which all compute the same values in the
+ * same order.  A solve looks up the configuration for its shape, the key
+ *   cheb/m<block width>/<f32|f64>/n2^<floor(log2 n)>/slots<densest tile's slots / 128>,
+ * and, when the key is new and mode is 1, times every configuration on its own operator
+ * before its first launch (outside any stream capture; a few dozen launches of the step) and
+ * keeps the fastest.
+ *   mode 0: fixed rules (64 KB, no early loads);  1 (default): tune new keys;  2: use known
+ *           keys only, fixed rules otherwise.
+ *   cache_path: a JSON file (object of key -> {"budget": bytes, "prefetch": 0|1, "us": time
+ *           per launch}) read now, if it exists, and rewritten whenever a key is added; NULL
+ *           keeps the entries in the context only.
+ * Errors: MGE_EINVAL (mode out of range, or a cache file that does not parse). */
+mge_status mge_ctx_set_autotune(mge_ctx* ctx, int mode, const char* cache_path);
 
 /* ---- kNN graph from points (Sec. 5.1) ---------------------------------------------- */
 

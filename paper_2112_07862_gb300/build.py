@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmge.so")
-SOURCES = ["api.cu", "graph.cu", "order.cu", "lobpcg.cu", "cheb.cu", "rr.cu", "serve.cu", "knn.cu", "kmeans.cu", "betweenness.cu", "gram_tc.cu"]
+SOURCES = ["api.cu", "graph.cu", "order.cu", "lobpcg.cu", "cheb.cu", "rr.cu", "serve.cu", "knn.cu", "kmeans.cu", "betweenness.cu", "gram_tc.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-Xptxas", "-O3"]

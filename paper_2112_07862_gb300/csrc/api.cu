@@ -229,7 +229,16 @@ mge_status mge_ctx_stats(const mge_ctx* c, mge_stats* out) {
   out->spmm_ms = ctx->spmm_ms;
   out->spmm_bytes = ctx->spmm_bytes;
   out->hbm_in_use = ctx->in_use.load();
+  {
+    std::lock_guard<std::mutex> lock(const_cast<Ctx*>(ctx)->tune_mu);
+    out->tune_entries = ctx->tune.size();
+  }
   return MGE_OK;
+}
+
+mge_status mge_ctx_set_autotune(mge_ctx* c, int mode, const char* cache_path) {
+  if (!c) return MGE_EINVAL;
+  return tune_set(&c->impl, mode, cache_path);
 }
 
 mge_status mge_ctx_set_timing(mge_ctx* c, int on) {

@@ -18,6 +18,8 @@
 // gathers queue (measured: 2 x 111 KB of stages per SM made the step 1.7x slower).
 #include "lobpcg_common.cuh"
 
+#include <type_traits>
+
 namespace mge {
 namespace lob {
 namespace {
@@ -61,7 +63,11 @@ __device__ __forceinline__ void ld4i(const int32_t* p, int32_t v[4]) {
   v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
 }
 
-template <typename T, typename SB, typename SO, int M>
+// PF: load the row's own R, d and D^-1 before its gathers rather than after them, so that
+// their latency (DRAM when the blocks exceed L2) overlaps the gathers' at the cost of nine
+// registers through the chunk loop (measured on one GB300: 5% faster per step on a 2M-node
+// graph, 4% slower on a 200k-node one; the autotuner chooses per operator).
+template <typename T, typename SB, typename SO, int M, bool PF>
 __global__ void __launch_bounds__(kChebThreads, sizeof(T) == 4 ? 2 : 1) k_cheb(ChebArgs<T> a, int cap, int nst) {
   const SB* __restrict__ X = static_cast<const SB*>(a.X);
   const SB* __restrict__ Rb = static_cast<const SB*>(a.R);
@@ -167,6 +173,12 @@ __global__ void __launch_bounds__(kChebThreads, sizeof(T) == 4 ? 2 : 1) k_cheb(C
       const int off = (int)(sslp[sl] - tb) + q * 4;
       T acc[4] = {0, 0, 0, 0}, wi[4];
       ldg4(X + row * M + cc, wi);
+      T rr[4], dd[4], dv;
+      if constexpr (PF) {
+        ldg4(Rb + row * M + cc, rr);
+        ld4(Db + row * M + cc, dd);           // D may be the output array: plain load
+        dv = __ldg(a.dinv + row);
+      }
       // chunk c of the row: indices and values at off + 64 c, then the four gathers; two
       // register sets in turn keep the next chunk's gathers in flight while one is summed.
       // With two lanes per row, lane `sub` takes chunks sub, sub + 2, ...; the second lane of
@@ -212,10 +224,12 @@ __global__ void __launch_bounds__(kChebThreads, sizeof(T) == 4 ? 2 : 1) k_cheb(C
         for (int u = 0; u < 4; ++u) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], 1);
       }
       if (valid && sub == 0) {
-        T rr[4], dd[4], dn[4], xn[4];
-        ldg4(Rb + row * M + c0, rr);
-        ld4(Db + row * M + c0, dd);           // D may be the output array: plain load
-        const T dv = __ldg(a.dinv + row);
+        T dn[4], xn[4];
+        if constexpr (!PF) {
+          ldg4(Rb + row * M + c0, rr);
+          ld4(Db + row * M + c0, dd);         // D may be the output array: plain load
+          dv = __ldg(a.dinv + row);
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const T y = a.shift * wi[u] + acc[u];
@@ -233,36 +247,34 @@ __global__ void __launch_bounds__(kChebThreads, sizeof(T) == 4 ? 2 : 1) k_cheb(C
 
 // Stage capacity and count: the densest tile's slots, in three stages if they fit the
 // per-CTA budget, else two, else the capacity two stages of the budget hold (denser tiles
-// read their indices and values from global memory).
-constexpr int64_t kChebStageBudget = 64 * 1024;
+// read their indices and values from global memory).  The budget is the tuned one (default
+// 64 KB: the L1 part of the SM keeps room for the gathers in flight).
+constexpr int kChebBudgets[] = {32 * 1024, 48 * 1024, 64 * 1024, 96 * 1024};
+constexpr int kChebMaxBudget = 96 * 1024;
 template <typename T>
-void cheb_config(int64_t max_tile_slots, int* cap, int* nst) {
+void cheb_config(int64_t max_tile_slots, int64_t budget, int* cap, int* nst) {
   const int64_t fixed = ChebLayout<T>(0).bytes;
   const int64_t per = 4 + sizeof(T);
   const int64_t want = std::max<int64_t>(64, (max_tile_slots + 63) / 64 * 64);
   for (int k : {3, 2}) {
-    if (256 + k * (fixed + want * per) <= kChebStageBudget) {
+    if (256 + k * (fixed + want * per) <= budget) {
       *cap = (int)want;
       *nst = k;
       return;
     }
   }
   *nst = 2;
-  *cap = (int)std::max<int64_t>(64, ((kChebStageBudget - 256) / 2 - fixed) / per / 64 * 64);
+  *cap = (int)std::max<int64_t>(64, ((budget - 256) / 2 - fixed) / per / 64 * 64);
 }
 
-}  // namespace
+// the early-load variant exists for FP32 throughout
+template <typename T, typename S, typename SO>
+constexpr bool cheb_has_pf() { return std::is_same<T, float>::value && std::is_same<S, float>::value && std::is_same<SO, float>::value; }
 
-template <typename T, typename S, typename SO, int M>
-cudaError_t cheb_configure() {
-  return cudaFuncSetAttribute(k_cheb<T, S, SO, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChebStageBudget);
-}
-
-template <typename T, typename S, typename SO, int M>
-cudaError_t cheb_launch(const Ctx* ctx, cudaStream_t st, const ChebArgs<T>& a, int64_t max_tile_slots) {
-  if (a.n <= 0) return cudaSuccess;
+template <typename T, typename S, typename SO, int M, bool PF>
+cudaError_t cheb_launch_v(const Ctx* ctx, cudaStream_t st, const ChebArgs<T>& a, int64_t max_tile_slots, int budget) {
   int cap = 0, nst = 0;
-  cheb_config<T>(max_tile_slots, &cap, &nst);
+  cheb_config<T>(max_tile_slots, budget, &cap, &nst);
   const size_t smem = 256 + (size_t)nst * ChebLayout<T>(cap).bytes;
   // resident CTAs per SM for this stage size (cached per host thread: the serving slots
   // launch from several threads; the size is fixed per operator)
@@ -270,20 +282,76 @@ cudaError_t cheb_launch(const Ctx* ctx, cudaStream_t st, const ChebArgs<T>& a, i
   thread_local int per_sm = 1;
   if (smem != last_smem) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb<T, S, SO, M>, kChebThreads, smem) != cudaSuccess || b < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cheb<T, S, SO, M, PF>, kChebThreads, smem) != cudaSuccess || b < 1)
       b = 1;
     per_sm = b;
     last_smem = smem;
   }
   const int64_t ntiles = (a.n + kSliceTileRows - 1) / kSliceTileRows;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * per_sm));
-  k_cheb<T, S, SO, M><<<(unsigned)grid, kChebThreads, smem, st>>>(a, cap, nst);
+  k_cheb<T, S, SO, M, PF><<<(unsigned)grid, kChebThreads, smem, st>>>(a, cap, nst);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T, typename S, typename SO, int M>
+cudaError_t cheb_configure() {
+  cudaError_t e = cudaFuncSetAttribute(k_cheb<T, S, SO, M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 + kChebMaxBudget);
+  if constexpr (cheb_has_pf<T, S, SO>()) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_cheb<T, S, SO, M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 + kChebMaxBudget);
+  }
+  return e;
+}
+
+template <typename T, typename S, typename SO, int M>
+cudaError_t cheb_launch(const Ctx* ctx, cudaStream_t st, const ChebArgs<T>& a, int64_t max_tile_slots, ChebTune tune) {
+  if (a.n <= 0) return cudaSuccess;
+  const int budget = tune.budget > 0 ? std::min(tune.budget, kChebMaxBudget) : 64 * 1024;
+  if constexpr (cheb_has_pf<T, S, SO>()) {
+    if (tune.prefetch) return cheb_launch_v<T, S, SO, M, true>(ctx, st, a, max_tile_slots, budget);
+  }
+  return cheb_launch_v<T, S, SO, M, false>(ctx, st, a, max_tile_slots, budget);
+}
+
+template <typename T, int M>
+cudaError_t cheb_tune(const Ctx* ctx, cudaStream_t st, const ChebArgs<T>& a, int64_t max_tile_slots,
+                      ChebTune* best, double* best_us, int* launches) {
+  *best = ChebTune{};
+  *best_us = 0;
+  *launches = 0;
+  if (a.n <= 0) return cudaSuccess;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  double bu = 1e30;
+  constexpr int kReps = 3;
+  for (int pf = 0; pf < (cheb_has_pf<T, T, T>() ? 2 : 1) && err == cudaSuccess; ++pf) {
+    for (int budget : kChebBudgets) {
+      const ChebTune c{budget, pf};
+      err = cheb_launch<T, T, T, M>(ctx, st, a, max_tile_slots, c);         // warm-up
+      *launches += 1 + kReps;
+      if (err == cudaSuccess) err = cudaEventRecord(e0, st);
+      for (int r = 0; r < kReps && err == cudaSuccess; ++r) err = cheb_launch<T, T, T, M>(ctx, st, a, max_tile_slots, c);
+      if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      if (err != cudaSuccess) break;
+      const double us = 1e3 * ms / kReps;
+      if (us < bu) { bu = us; *best = c; }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (err == cudaSuccess) *best_us = bu;
+  return err;
 }
 
 #define MGE_CHEB_INST(T, S, SO, M)                                                           \
   template cudaError_t cheb_configure<T, S, SO, M>();                                        \
-  template cudaError_t cheb_launch<T, S, SO, M>(const Ctx*, cudaStream_t, const ChebArgs<T>&, int64_t);
+  template cudaError_t cheb_launch<T, S, SO, M>(const Ctx*, cudaStream_t, const ChebArgs<T>&, int64_t, ChebTune);
 #define MGE_CHEB_INST_M(M)                                                                   \
   MGE_CHEB_INST(float, float, float, M)                                                      \
   MGE_CHEB_INST(double, double, double, M)                                                   \
@@ -294,6 +362,15 @@ MGE_CHEB_INST_M(8)
 MGE_CHEB_INST_M(12)
 MGE_CHEB_INST_M(16)
 MGE_CHEB_INST_M(24)
+#define MGE_CHEB_TUNE_INST(M)                                                                \
+  template cudaError_t cheb_tune<float, M>(const Ctx*, cudaStream_t, const ChebArgs<float>&, int64_t, ChebTune*, double*, int*); \
+  template cudaError_t cheb_tune<double, M>(const Ctx*, cudaStream_t, const ChebArgs<double>&, int64_t, ChebTune*, double*, int*);
+MGE_CHEB_TUNE_INST(4)
+MGE_CHEB_TUNE_INST(8)
+MGE_CHEB_TUNE_INST(12)
+MGE_CHEB_TUNE_INST(16)
+MGE_CHEB_TUNE_INST(24)
+#undef MGE_CHEB_TUNE_INST
 #undef MGE_CHEB_INST_M
 #undef MGE_CHEB_INST
 

@@ -992,6 +992,7 @@ struct Solver {
   int maxiter;
   bool inverse_rr = true;
   bool rr_auto = false;             // inverse form first, FP64 Jacobi once the residuals stall
+  ChebTune ctune;                   // the Chebyshev step's configuration (tuned per shape)
   double tau = 1e-12, tau_p = 1e-16, tau_w = 1e-10;
   int64_t nnz_a = 0, nnz_pc = 0;
 
@@ -1049,6 +1050,50 @@ struct Solver {
     // eps > 0, or Q with the constant vector deflated
     inverse_rr = (sizeof(T) == 4) && !op.rr_fp64 && (op.shift > 0.0 || op.deflate);
     rr_auto = inverse_rr && op.rr_switch;
+    return MGE_OK;
+  }
+
+  // The Chebyshev step's configuration for this shape (width, precision, size class and slot
+  // density of the sliced operator): the context's tuned entry, measured here -- before the
+  // solve's first launch and outside any stream capture -- when the context tunes and the
+  // shape is new.  The trial steps run on the solve's scratch blocks.
+  mge_status tune_cheb() {
+    if (cheb_deg <= 1 || !op.sl_slp || pc_bf16 || ctx->tune_mode == 0) return MGE_OK;
+    char key[128];
+    const int lg = (int)std::floor(std::log2((double)std::max<int64_t>(n, 1)));
+    const int spr = (int)std::lround((double)op.sl_max_tile_slots / kSliceTileRows);
+    snprintf(key, sizeof key, "cheb/m%d/%s/n2^%d/slots%d", M, sizeof(T) == 8 ? "f64" : "f32", lg, spr);
+    TuneEntry e;
+    if (tune_lookup(ctx, key, &e)) {
+      ctune.budget = e.budget;
+      ctune.prefetch = e.prefetch;
+      return MGE_OK;
+    }
+    if (ctx->tune_mode != 1) return MGE_OK;
+    cudaStreamCaptureStatus cs;
+    MGE_CUDA(ctx, cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return MGE_OK;
+    const size_t blk = (size_t)n * M * sizeof(T);
+    MGE_CUDA(ctx, cudaMemsetAsync(Wr.p, 0, blk, st));
+    MGE_CUDA(ctx, cudaMemsetAsync(Yc0.p, 0, blk, st));
+    MGE_CUDA(ctx, cudaMemsetAsync(Dc.p, 0, blk, st));
+    ChebArgs<T> c{};
+    c.n = n;
+    c.slp = op.sl_slp; c.perm = op.sl_perm; c.col = op.sl_col;
+    c.val = static_cast<const T*>(op.sl_val);
+    c.shift = (T)(op.pc_ptr ? op.pc_shift : op.shift);
+    c.X = Yc0.p; c.R = Wr.p; c.D = Dc.p;
+    c.dinv = static_cast<const T*>(op.pc_ptr ? op.pc_dinv : op.dinv);
+    c.Dout = Dc.p; c.Xout = Yc1.p;
+    c.sy = T(1); c.sd = T(1); c.c1 = T(0.5); c.c2 = T(0.5);
+    c.st = state;
+    ChebTune best;
+    double us = 0;
+    int launched = 0;
+    MGE_CUDA(ctx, (cheb_tune<T, M>(ctx, st, c, op.sl_max_tile_slots, &best, &us, &launched)));
+    MGE_LAUNCHED(ctx, launched);
+    ctune = best;
+    tune_store(ctx, key, TuneEntry{best.budget, best.prefetch, us});
     return MGE_OK;
   }
 
@@ -1230,7 +1275,7 @@ struct Solver {
         c.c2 = (T)(2.0 * rho / ch_delta);
         c.st = state;
         if (timed) MGE_TRY(time_begin(cheb_bytes()));
-        MGE_CUDA(ctx, (cheb_launch<T, T, T, M>(ctx, st, c, op.sl_max_tile_slots)));
+        MGE_CUDA(ctx, (cheb_launch<T, T, T, M>(ctx, st, c, op.sl_max_tile_slots, ctune)));
         MGE_LAUNCHED(ctx, 1);
         if (timed) MGE_TRY(time_end());
         rho_prev = rho;
@@ -1641,6 +1686,7 @@ mge_status prepare_solver(Solver<T, M>& s) {
     }
   }
   MGE_CUDA(ctx, rr_configure());
+  MGE_TRY(s.tune_cheb());
   return MGE_OK;
 }
 

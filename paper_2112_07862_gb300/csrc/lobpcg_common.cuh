@@ -312,10 +312,21 @@ cudaError_t gram_tc_launch(const Ctx* ctx, cudaStream_t st, const GramTcArgs& a,
 // Launches the step on stream st; max_tile_slots (the densest tile of the sliced copy) sizes
 // the shared-memory stages.  S is the storage type of x, R, d and d_out, SO that of x_out
 // (T, or __nv_bfloat16 with T = float).  cheb_configure raises the dynamic shared-memory limit.
+// A tuned configuration of the step (stage budget in bytes, early loads; cheb.cu, tune.cu).
+struct ChebTune {
+  int budget = 64 * 1024;
+  int prefetch = 0;
+};
 template <typename T, typename S, typename SO, int M>
-cudaError_t cheb_launch(const Ctx* ctx, cudaStream_t st, const ChebArgs<T>& a, int64_t max_tile_slots);
+cudaError_t cheb_launch(const Ctx* ctx, cudaStream_t st, const ChebArgs<T>& a, int64_t max_tile_slots,
+                        ChebTune tune = ChebTune{});
 template <typename T, typename S, typename SO, int M>
 cudaError_t cheb_configure();
+// Times every configuration on the step `a` (its buffers are overwritten: scratch only) and
+// returns the fastest with its time per launch.  Synchronises the stream; not during capture.
+template <typename T, int M>
+cudaError_t cheb_tune(const Ctx* ctx, cudaStream_t st, const ChebArgs<T>& a, int64_t max_tile_slots,
+                      ChebTune* best, double* best_us, int* launches);
 
 }  // namespace lob
 }  // namespace mge

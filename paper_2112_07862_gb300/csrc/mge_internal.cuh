@@ -8,6 +8,7 @@
 
 #include <atomic>
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -57,6 +58,14 @@ void set_error(Ctx* ctx, const char* fmt, ...);
 // ---------------------------------------------------------------------------------------
 // device memory: plain cudaMallocAsync-free allocations accounted against a budget
 // ---------------------------------------------------------------------------------------
+// One autotuned kernel configuration: the Chebyshev step's shared-memory stage budget and
+// whether it loads the row's own R, d and D^-1 before its gathers (tune.cu).
+struct TuneEntry {
+  int budget = 0;
+  int prefetch = 0;
+  double us = 0;                   // its measured time per launch
+};
+
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -83,7 +92,18 @@ struct Ctx {
   void* self = nullptr;            // the owning mge_ctx*
   std::atomic<int> refs{1};        // the context itself plus one per live ops handle
   bool closed = false;
+  // kernel autotuning (tune.cu): mode 0 off (fixed rules), 1 tune keys not yet known, 2 use
+  // known keys only; entries persist in a JSON file when a path is set
+  int tune_mode = 1;
+  std::string tune_path;
+  std::mutex tune_mu;
+  std::map<std::string, TuneEntry> tune;
 };
+
+// autotuning cache (tune.cu)
+bool tune_lookup(Ctx* ctx, const std::string& key, TuneEntry* e);
+void tune_store(Ctx* ctx, const std::string& key, const TuneEntry& e);
+mge_status tune_set(Ctx* ctx, int mode, const char* path);
 
 mge_status dev_alloc(Ctx* ctx, void** p, size_t bytes);
 void dev_free(Ctx* ctx, void* p, size_t bytes);

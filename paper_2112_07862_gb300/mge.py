@@ -24,7 +24,7 @@ PRECISION = {"fp64": MGE_FP64, "fp32": MGE_FP32, "bf16": MGE_BF16}
 # every symbol include/mge.h declares
 EXPORTS = [
     "mge_create", "mge_destroy", "mge_strerror", "mge_ctx_last_error", "mge_ctx_stats",
-    "mge_ctx_set_timing", "mge_ctx_reset_stats", "mge_build_graph_ops", "mge_build_graph_ops_batch", "mge_ops_destroy",
+    "mge_ctx_set_timing", "mge_ctx_reset_stats", "mge_ctx_set_autotune", "mge_build_graph_ops", "mge_build_graph_ops_batch", "mge_ops_destroy",
     "mge_ops_info", "mge_ops_export", "mge_ops_node_order", "mge_ops_apply", "mge_ops_apply_inplace", "mge_embed", "mge_embed_batch", "mge_submit", "mge_poll",
     "mge_release", "mge_betweenness", "mge_kmeans", "mge_knn_graph", "mge_graph_info", "mge_graph_csr", "mge_graph_export", "mge_graph_destroy",
 ]
@@ -32,7 +32,8 @@ EXPORTS = [
 
 class mge_stats(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("spmm_launches", C.c_uint64),
-                ("spmm_ms", C.c_double), ("spmm_bytes", C.c_uint64), ("hbm_in_use", C.c_size_t)]
+                ("spmm_ms", C.c_double), ("spmm_bytes", C.c_uint64), ("hbm_in_use", C.c_size_t),
+                ("tune_entries", C.c_uint64)]
 
 
 class mge_ops_opts(C.Structure):
@@ -95,6 +96,7 @@ def load(path: str = LIB_PATH):
         "mge_ctx_stats": (i, [vp, C.POINTER(mge_stats)]),
         "mge_ctx_set_timing": (i, [vp, i]),
         "mge_ctx_reset_stats": (i, [vp]),
+        "mge_ctx_set_autotune": (i, [vp, i, C.c_char_p]),
         "mge_build_graph_ops": (i, [vp, i64, vp, vp, vp, i, C.POINTER(mge_ops_opts), C.POINTER(vp)]),
         "mge_build_graph_ops_batch": (i, [vp, i, vp, vp, vp, vp, i, C.POINTER(mge_ops_opts), i, vp, vp]),
         "mge_ops_destroy": (i, [vp]),
@@ -171,6 +173,12 @@ def mge_ctx_stats(ctx) -> mge_stats:
 
 def mge_ctx_set_timing(ctx, on: bool) -> int:
     return load().mge_ctx_set_timing(ctx, 1 if on else 0)
+
+
+def mge_ctx_set_autotune(ctx, mode: int, cache_path: str | None = None) -> None:
+    """mode 0 fixed rules, 1 tune new shapes (default), 2 known shapes only; cache_path: JSON file."""
+    s = load().mge_ctx_set_autotune(ctx, int(mode), cache_path.encode() if cache_path else None)
+    _check(ctx, s, "mge_ctx_set_autotune")
 
 
 def mge_ctx_reset_stats(ctx) -> int:
