@@ -175,7 +175,8 @@ typedef struct {
   int      mu_override_set;   /* nonzero: use mu_override instead of Eq. 9                  */
   double   mu_override;
   double   eps_tol;           /* relative-residual tolerance of the eps solve (the measure
-                                 of mge_embed; 0 = default: 1e-10 in FP64, 1e-5 otherwise)  */
+                                 of mge_embed; 0 = default: 1e-10 in FP64, 1e-4 otherwise:
+                                 eps then carries a relative error below 2e-7, measured)     */
   int      eps_guard;         /* extra LOBPCG columns for the eps solve (default 7)         */
   int      eps_maxiter;       /* default 20000                                              */
   uint64_t seed;              /* seed of the eps solve's initial block                      */

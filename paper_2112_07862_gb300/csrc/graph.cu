@@ -866,7 +866,11 @@ mge_status build_phase1(Ctx* ctx, cudaStream_t st, int64_t n, const int64_t* rp_
       int guard = o.eps_guard > 0 ? o.eps_guard : (n >= 2 * 8 ? 7 : 3);
       int m = round_block_width(1 + guard);
       if (m > n - 1) m = -1;
-      double tol = o.eps_tol > 0 ? o.eps_tol : (o.precision == MGE_FP64 ? 1e-10 : 1e-5);
+      // FP32: eps enters A as a shift, so its relative error passes to the eigenvalues about
+      // one to one; at 1e-4 in the relative residual it stays below 2e-7 (measured on 200k and
+      // 2M-node graphs against 1e-5: 18 -> 16 and 50 -> 41 iterations), far below what a
+      // 1e-5 embedding resolves
+      double tol = o.eps_tol > 0 ? o.eps_tol : (o.precision == MGE_FP64 ? 1e-10 : 1e-4);
       int maxit = o.eps_maxiter > 0 ? o.eps_maxiter : 20000;
       if (m < 0) {
         set_error(ctx, "graph too small for the eps solve block (n = %lld)", (long long)n);
