@@ -45,8 +45,8 @@ def accuracy_note(a):
     """Where the accuracy of this workload's results is checked."""
     w = (a.shape, a.n, a.knn, a.K, a.seed)
     if w == ("swiss_roll", 200_000, 10, 8, 2) and a.precision in ("fp32", "bf16"):
-        return ("eigenvalues within 1.2e-6 relative and eigenvectors within 1.4e-4 rad of the oracle's "
-                "machine-precision pairs on this workload (tests/test_gpu_fullsize.py)")
+        return ("eigenvalues within 1.9e-6 relative and eigenvectors within 1.6e-6 rad (FP32; BF16 form 2.9e-6, "
+                "3.1e-5 rad) of the oracle's machine-precision pairs on this workload (tests/test_gpu_fullsize.py)")
     if w == ("sphere", 2_000_000, 10, 16, 3) and a.precision == "fp32":
         return ("pairs checked by properties at this size (tests/test_gpu_sphere_2m.py): backward error <= 1e-6 "
                 "against the oracle's FP64 A and b, V^T B V = I, the sphere's 1-3-5-7 eigenvalue groups, eps "
