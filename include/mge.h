@@ -176,7 +176,7 @@ typedef struct {
   double   mu_override;
   double   eps_tol;           /* relative-residual tolerance of the eps solve (the measure
                                  of mge_embed; 0 = default: 1e-10 in FP64, 1e-4 otherwise:
-                                 eps then carries a relative error below 2e-7, measured)     */
+                                 eps then carries a relative error below 1e-6, measured)     */
   int      eps_guard;         /* extra LOBPCG columns for the eps solve (default 7)         */
   int      eps_maxiter;       /* default 20000                                              */
   uint64_t seed;              /* seed of the eps solve's initial block                      */
