@@ -82,6 +82,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the kNN, k-means and betweenness lines")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-sphere-2m", action="store_true", help="skip the 2M-node sphere (K = 16) line")
+    p.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                   help="1: the Chebyshev step's autotuner (default); 0: its fixed rule, for comparison")
     p.add_argument("--autotune-cache", default=None,
                    help="JSON cache of the Chebyshev step's tuned configurations shared by the bench's contexts "
                         "(default: a new temporary file); read first if it exists")
@@ -219,7 +221,7 @@ def run_ours(a, dist):
     ctx = mge.Context(dist.local)
     # the Chebyshev step's configurations tuned during the warm-up, reported with the line
     tune_path = tune_cache(a)
-    mge.mge_ctx_set_autotune(ctx.h, 1, tune_path)
+    mge.mge_ctx_set_autotune(ctx.h, a.autotune, tune_path)
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
     # device-resident inputs for the kernel-level number
@@ -389,7 +391,7 @@ def run_batch(a):
     nodes = sum(P.shape[0] for P, _, _ in specs)
     Ks = [K for _, _, K in specs]
     with mge.Context(0) as ctx:
-        mge.mge_ctx_set_autotune(ctx.h, 1, tune_cache(a))
+        mge.mge_ctx_set_autotune(ctx.h, a.autotune, tune_cache(a))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         graphs = [mge.mge_knn_graph(ctx.h, P, k) for P, k, _ in specs]
@@ -477,7 +479,7 @@ def run_serving(a):
     import threading
     budget = int(a.serve_budget_gb * (1 << 30))
     with mge.Context(0, budget) as ctx:
-        mge.mge_ctx_set_autotune(ctx.h, 2, tune_cache(a))
+        mge.mge_ctx_set_autotune(ctx.h, 2 * a.autotune, tune_cache(a))
         # one small request first, so that the slots and their streams exist
         P0 = np.ascontiguousarray(mg.sample_points("square", 1_000, 499))
         t = mge.mge_submit(ctx.h, request(P0, 2, mge.MGE_FP32))
@@ -580,7 +582,7 @@ def run_sphere_2m(a):
     sptr = stream.cuda_stream
     tune_path = tune_cache(a)
     with mge.Context(0) as ctx:
-        mge.mge_ctx_set_autotune(ctx.h, 1, tune_path)
+        mge.mge_ctx_set_autotune(ctx.h, a.autotune, tune_path)
         P = torch.from_numpy(np.ascontiguousarray(mg.sample_points("sphere", n, seed))).cuda()
         g = mge.mge_knn_graph(ctx.h, P, k, stream=sptr)
         rp, col, w = mge.mge_graph_csr(g)
