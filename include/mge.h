@@ -182,7 +182,8 @@ typedef struct {
   uint64_t seed;              /* seed of the eps solve's initial block                      */
   void*    stream;            /* cudaStream_t or NULL                                       */
   int      eps_precond_degree; /* Chebyshev preconditioner degree of the eps solve (see
-                                 mge_embed_opts.precond_degree; 0 = default 24)              */
+                                 mge_embed_opts.precond_degree; 0 = default
+                                 round(sqrt(n) / 12) within [8, 32]; at most 256)            */
   int      keep_order;        /* 0 (default): the library renumbers the nodes internally into
                                  a locality order (compact patches of the graph in
                                  consecutive rows, so that the SpMMs' gathers share cache
@@ -318,13 +319,16 @@ typedef struct {
                                  d = 1 is the Jacobi preconditioner; each degree above 1
                                  costs one SpMM of L' per iteration and cuts the iteration
                                  count about in proportion.  The paper leaves the
-                                 preconditioner open.  0 = default 64; at most 64.          */
+                                 preconditioner open.  0 = default round(sqrt(n) / 5)
+                                 within [16, 64] (measured best on 2k-50k-node graphs
+                                 and at 200k nodes); at most 256.  MGE_BF16 caps it at 8.  */
   int         rr_fp64;        /* arithmetic of the Rayleigh-Ritz eigensolve and of the
                                  Cholesky that B-normalises W, for FP32 blocks:
                                   0 (default) the inverse-pencil FP32 solve described under
                                     MGE_FP32 until the largest relative residual of the K
-                                    wanted pairs has not halved for 10 iterations, then
-                                    cyclic Jacobi in FP64 for the rest of the solve;
+                                    wanted pairs, once within 1000x of tol, has not halved
+                                    for 10 iterations, then cyclic Jacobi in FP64 for the
+                                    rest of the solve;
                                   1 cyclic Jacobi on the 3m x 3m pencil in FP64 throughout;
                                  -1 the FP32 form throughout.
                                  The FP32 form's eigenvectors carry errors of about u
