@@ -125,7 +125,7 @@ def lobpcg(A, b: np.ndarray, K: int, *, guard: int = 0, Y=None, tol: float = 1e-
            normA: float | None = None, measure: str = "backward") -> EigResult:
     """Textbook FP64 LOBPCG for the K smallest eigenpairs of (A, diag(b)).
 
-    m = K + guard columns are iterated; convergence is judged on the first K by the
+    m = K + guard columns are iterated; convergence is tested on the first K by the
     backward error eta <= tol (measure="backward") or by the relative residual
     rho <= tol (measure="relative", see ``relative_residuals``).
     """
